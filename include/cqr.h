@@ -1,0 +1,169 @@
+/*
+ * cqr.h - C ABI of the GB300 (sm_103a) FP64 CholeskyQR library.
+ *
+ * QR factorisation A = Q R of tall-and-skinny FP64 matrices (m >= n) by the
+ * modified CholeskyQR2 with block Gram-Schmidt (mCQR2GS, arXiv 2405.04237,
+ * Sec. 5.4, Alg. 9), CholeskyQR2 with Gram-Schmidt (CQR2GS, Sec. 5.3, Alg. 6
+ * and Alg. 7), CholeskyQR2 (Sec. 4, Alg. 3) and shifted CholeskyQR3 (Sec. 5.2,
+ * Alg. 4 and Alg. 5), plus the reverse-mode adjoint of A = Q R.
+ *
+ * Conventions shared by every entry point
+ *   - All matrices are FP64, column-major, with leading dimension >= rows.
+ *   - Matrix and workspace pointers are DEVICE pointers owned by the caller
+ *     (except where an argument says "host").  The library never allocates
+ *     device memory: the caller passes a workspace of at least the size the
+ *     matching *_workspace_size() function returns, 256-byte aligned.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and returns without synchronising.  Every launch is
+ *     asynchronous and graph-capturable: no allocation, no host sync.
+ *   - The return value reports argument errors only, LAPACK style: 0 = ok,
+ *     -i = argument i (1-based) invalid; CQR_ERR_CUDA if a launch failed.
+ *     Numerical failure (a Cholesky breakdown: the Gram matrix is not
+ *     numerically positive definite, Sec. 3) is reported through a device
+ *     status word kept at the start of the workspace; read it with
+ *     cqr_read_status() (synchronous) after the stream work completes.
+ *     Status codes: 0 = ok; j+1 (> 0) = breakdown at global column j of the
+ *     factorisation; CQR_STATUS_TIMEOUT = a bounded wait of the batched
+ *     persistent kernel expired.  After a breakdown, every later kernel of
+ *     the same call returns immediately and Q, R are undefined.
+ */
+#ifndef CQR_GB300_H
+#define CQR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cqr_stream_t; /* identical to cudaStream_t */
+
+enum cqr_variant {
+  CQR_MCQR2GS = 0, /* Alg. 9: CQR2 on panel 1, then per panel: project, CQR, re-orthogonalise, CQR */
+  CQR_CQR2GS = 1,  /* Alg. 7: CQRGS (Alg. 6) twice, R = R2 R1 */
+  CQR_CQR2 = 2,    /* Alg. 3: CholeskyQR twice on the whole matrix (panel_b ignored, b = n) */
+  CQR_SCQR3 = 3    /* Alg. 5: shifted CholeskyQR (Alg. 4) then CholeskyQR2, R = R2 R1 (b = n) */
+};
+
+#define CQR_ERR_CUDA (-1000)
+#define CQR_STATUS_TIMEOUT (-2000)
+
+/* Largest panel width the library accepts (the one-CTA Cholesky keeps a
+ * b x b Gram matrix in shared memory up to 128 and in L2 above). */
+#define CQR_MAX_PANEL 512
+
+/*
+ * cqr_workspace_size: bytes of device workspace cqr_factor() needs for an
+ * m x n factorisation with panel width panel_b (0 = library default, see
+ * cqr_default_panel) and the given variant.  Returns 0 for invalid sizes.
+ */
+size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant);
+
+/*
+ * cqr_default_panel: the panel width used when panel_b == 0: the largest
+ * divisor of n that is <= min(256, ceil(n/3)), i.e. at least three panels,
+ * the count the paper found stable for condition numbers up to 1e15
+ * (Sec. 5.4, Fig. 6), and a divisor so that k = n/b is an integer (Alg. 6).
+ */
+int cqr_default_panel(int64_t n);
+
+/*
+ * cqr_factor: A = Q R.
+ *   m, n       rows and columns, m >= n >= 1                       (args 1, 2)
+ *   A, lda     input, m x n, lda >= m.  Read-only unless Q == A    (args 3, 4)
+ *   panel_b    panel width b; must divide n; 0 = cqr_default_panel(n).
+ *              Ignored by CQR_CQR2 and CQR_SCQR3 (b = n)            (arg 5)
+ *   Q, ldq     output m x n with orthonormal columns, ldq >= m.  Q may be
+ *              A itself (in-place factorisation, ldq == lda); otherwise Q
+ *              must not overlap A                                   (args 6, 7)
+ *   R, ldr     output n x n upper triangular with positive diagonal;
+ *              its strict lower triangle is zeroed; ldr >= n        (args 8, 9)
+ *   variant    enum cqr_variant                                     (arg 10)
+ *   workspace  device buffer of ws_bytes >= cqr_workspace_size()    (args 11, 12)
+ *   stream     CUDA stream                                          (arg 13)
+ * Panel loop (Alg. 9): for each panel j the Gram W_j = A_j^T A_j (Alg. 1
+ * step 1), the b x b Cholesky W_j = U^T U (step 2), the triangular solve
+ * Q_j = A_j U^{-1} (step 3), the projection Y = Q_{j-1}^T A_{j:k} and the
+ * update A_{j:k} -= Q_{j-1} Y (Alg. 9 steps 3-4), and the interleaved
+ * CQR / re-orthogonalisation / CQR of the panel (Alg. 9 steps 6-8), with
+ * R_jj = S2 S1 and R_{1:j-1,j} += Z S1.
+ */
+int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
+               int64_t ldr, int variant, void* workspace, size_t ws_bytes, cqr_stream_t stream);
+
+/*
+ * cqr_read_status: synchronises `stream`, then copies the status word of the
+ * last call that used `workspace` into *status (host).  Returns 0, or
+ * CQR_ERR_CUDA if the copy failed.
+ */
+int cqr_read_status(const void* workspace, cqr_stream_t stream, int* status);
+
+/*
+ * cqr_backward_workspace_size: device workspace bytes cqr_backward() needs.
+ */
+size_t cqr_backward_workspace_size(int64_t m, int64_t n);
+
+/*
+ * cqr_backward: reverse-mode adjoint of A = Q R (not in the paper; the
+ * standard QR rule):  M = R Rbar^T - Qbar^T Q;  B = Qbar + Q copyltu(M),
+ * copyltu(M) = tril(M) + tril(M,-1)^T;  Abar = B R^{-T} (row-wise
+ * substitution against R^T).
+ *   m, n       sizes, m >= n >= 1                                   (args 1, 2)
+ *   Q, ldq     forward output Q (m x n)                             (args 3, 4)
+ *   R, ldr     forward output R (n x n upper, nonsingular)          (args 5, 6)
+ *   dQ, lddq   upstream gradient Qbar (m x n); NULL means zero      (args 7, 8)
+ *   dR, lddr   upstream gradient Rbar (n x n); NULL means zero;
+ *              only its upper triangle influences the result        (args 9, 10)
+ *   dA, ldda   output Abar (m x n); must not overlap the inputs     (args 11, 12)
+ *   workspace, ws_bytes, stream  as in cqr_factor                  (args 13-15)
+ * Uses the same Gram/projection, update and triangular-solve kernels as the
+ * forward pass.  The status word is not used (R is assumed nonsingular).
+ */
+int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const double* R, int64_t ldr,
+                 const double* dQ, int64_t lddq, const double* dR, int64_t lddr, double* dA, int64_t ldda,
+                 void* workspace, size_t ws_bytes, cqr_stream_t stream);
+
+/*
+ * cqr_batched_workspace_size: device workspace bytes for a batch, given the
+ * HOST arrays of sizes and panel widths (panel_b[i] == 0 = default).
+ */
+size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant);
+
+/*
+ * cqr_factor_batched: factors `batch` independent matrices A_i = Q_i R_i in
+ * one persistent launch sequence (Alg. 9 per matrix; variant must be
+ * CQR_MCQR2GS or CQR_CQR2GS).
+ *   batch                  number of matrices, >= 0                  (arg 1)
+ *   m, n, lda, panel_b     HOST arrays of length batch                (args 2-5)
+ *   A, Q, R                HOST arrays of DEVICE pointers; ldq_i = lda_i
+ *                          and ldr_i = n_i (Q_i may equal A_i)        (args 6-8)
+ *   variant                as in cqr_factor                          (arg 9)
+ *   status                 DEVICE int array of length batch: per-matrix
+ *                          status codes as in cqr_factor              (arg 10)
+ *   workspace, ws_bytes    >= cqr_batched_workspace_size()            (args 11, 12)
+ *   stream                 CUDA stream                               (arg 13)
+ * The descriptor table is copied to the workspace with one host-to-device
+ * copy per call, so for CUDA-graph replay the pointer arrays must be stable.
+ * Each matrix's result is identical (bitwise) to a cqr_factor() call with
+ * the same sizes and panel width.
+ */
+int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* lda, const int* panel_b,
+                       double* const* A, double* const* Q, double* const* R, int variant, int* status,
+                       void* workspace, size_t ws_bytes, cqr_stream_t stream);
+
+/* cqr_status_string: static description of a status or return code. */
+const char* cqr_status_string(int status);
+
+/*
+ * cqr_probe_fp64_peak: measures this GPU's FP64 FMA throughput (DFMA chains
+ * on every SM) for `iters` iterations and returns GFLOP/s (<= 0 on error).
+ * Synchronous.  Used to state the FP64 roofline the kernels run against.
+ */
+double cqr_probe_fp64_peak(int iters);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CQR_GB300_H */

@@ -1,0 +1,223 @@
+"""GB300-native FP64 CholeskyQR library (arXiv 2405.04237).
+
+QR factorisation A = Q R of tall-and-skinny FP64 matrices by the modified
+CholeskyQR2 with block Gram-Schmidt (mCQR2GS, Alg. 9), CQR2GS (Alg. 7),
+CholeskyQR2 (Alg. 3) and shifted CholeskyQR3 (Alg. 5), with a hand-written
+adjoint, a batched path and a panel-width autotuner.
+
+The compute runs in the CUDA library behind the C ABI of ``include/cqr.h``;
+this module only marshals torch tensors (device memory, the current stream)
+into that ABI.  There is no CPU fallback.
+
+Layout: the library is column-major.  A torch matrix with strides (1, ld) is
+passed as is; any other layout is copied to a column-major buffer first.
+Outputs are returned as column-major tensors (strides (1, m) and (1, n)).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _capi
+from ._capi import CQRError, VARIANTS, load, status_string
+
+__all__ = [
+    "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
+    "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "colmajor", "empty_colmajor",
+]
+
+
+def _variant(v) -> int:
+    if isinstance(v, str):
+        return VARIANTS[v.lower()]
+    return int(v)
+
+
+def colmajor(A: torch.Tensor) -> torch.Tensor:
+    """A column-major view of A if it already is one, else a column-major copy."""
+    if A.dim() != 2:
+        raise ValueError("expected a matrix")
+    m, n = A.shape
+    if A.stride(0) == 1 and (n <= 1 or A.stride(1) >= max(m, 1)):
+        return A
+    return A.t().contiguous().t()
+
+
+def empty_colmajor(m: int, n: int, device, dtype=torch.float64) -> torch.Tensor:
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def _ld(A: torch.Tensor) -> int:
+    m, n = A.shape
+    return max(A.stride(1) if n > 1 else m, m, 1)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_input(A: torch.Tensor):
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor (the library has no CPU path)")
+    if A.dtype != torch.float64:
+        raise ValueError("A must be float64")
+
+
+def default_panel(n: int) -> int:
+    return int(load().cqr_default_panel(int(n)))
+
+
+def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs") -> int:
+    return int(load().cqr_workspace_size(int(m), int(n), int(panel_b), _variant(variant)))
+
+
+def read_status(workspace: torch.Tensor, stream=None) -> int:
+    st = ctypes.c_int(0)
+    rc = load().cqr_read_status(_ptr(workspace), _stream(stream), ctypes.byref(st))
+    if rc != 0:
+        raise CQRError(rc, "cqr_read_status")
+    return int(st.value)
+
+
+def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: bool = False, check: bool = True,
+           out=None, workspace: torch.Tensor | None = None, stream=None):
+    """A = Q R.  Returns (Q, R) as column-major FP64 tensors.
+
+    inplace=True overwrites A's (column-major) storage with Q.  check=True
+    synchronises the stream and raises CQRError on a Cholesky breakdown; with
+    check=False the call is fully asynchronous (and graph-capturable when a
+    workspace and outputs are supplied).
+    """
+    _check_input(A)
+    L = load()
+    m, n = A.shape
+    var = _variant(variant)
+    Ac = colmajor(A)
+    if inplace and Ac.data_ptr() != A.data_ptr():
+        raise ValueError("inplace=True needs a column-major A")
+    if out is not None:
+        Q, R = out
+    else:
+        Q = Ac if inplace else empty_colmajor(m, n, A.device)
+        R = empty_colmajor(n, n, A.device)
+    ws_bytes = L.cqr_workspace_size(m, n, int(panel_b), var)
+    if ws_bytes == 0:
+        raise CQRError(-5 if n > 0 and m >= n else -1, "cqr_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=A.device)
+    elif workspace.numel() < ws_bytes:
+        raise ValueError(f"workspace too small: {workspace.numel()} < {ws_bytes}")
+    st = _stream(stream)
+    rc = L.cqr_factor(m, n, _ptr(Ac), _ld(Ac), int(panel_b), _ptr(Q), _ld(Q), _ptr(R), _ld(R), var,
+                      _ptr(workspace), ctypes.c_size_t(workspace.numel()), st)
+    if rc != 0:
+        raise CQRError(rc, "cqr_factor")
+    if check:
+        s = read_status(workspace, stream)
+        if s != 0:
+            raise CQRError(s, "cqr_factor")
+    return Q, R
+
+
+def backward(Q: torch.Tensor, R: torch.Tensor, dQ: torch.Tensor | None, dR: torch.Tensor | None, stream=None):
+    """Abar for A = QR: M = R Rbar^T - Qbar^T Q; Abar = (Qbar + Q copyltu(M)) R^{-T}."""
+    L = load()
+    m, n = Q.shape
+    Qc, Rc = colmajor(Q), colmajor(R)
+    dQc = colmajor(dQ) if dQ is not None else None
+    dRc = colmajor(dR) if dR is not None else None
+    dA = empty_colmajor(m, n, Q.device)
+    ws_bytes = L.cqr_backward_workspace_size(m, n)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=Q.device)
+    rc = L.cqr_backward(m, n, _ptr(Qc), _ld(Qc), _ptr(Rc), _ld(Rc), _ptr(dQc), _ld(dQc) if dQc is not None else m,
+                        _ptr(dRc), _ld(dRc) if dRc is not None else n, _ptr(dA), _ld(dA), _ptr(ws),
+                        ctypes.c_size_t(ws.numel()), _stream(stream))
+    if rc != 0:
+        raise CQRError(rc, "cqr_backward")
+    return dA
+
+
+class CQRFunction(torch.autograd.Function):
+    """Differentiable A -> (Q, R).  Saves only the outputs (Q, R): the adjoint
+    needs no per-panel intermediates, so nothing else is kept between the
+    forward and backward passes."""
+
+    @staticmethod
+    def forward(ctx, A, panel_b=0, variant="mcqr2gs"):
+        Q, R = factor(A.detach(), panel_b, variant)
+        ctx.save_for_backward(Q, R)
+        return Q, R
+
+    @staticmethod
+    def backward(ctx, dQ, dR):
+        Q, R = ctx.saved_tensors
+        return backward(Q, R, dQ, dR), None, None
+
+
+def qr(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs"):
+    """Differentiable QR (see CQRFunction)."""
+    return CQRFunction.apply(A, panel_b, variant)
+
+
+def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, stream=None, workspace=None,
+                   status=None, inplace: bool = False):
+    """Factor a list of column-major FP64 CUDA matrices in one batched call.
+
+    Returns a list of (Q_i, R_i).  Each result equals factor(A_i, b_i).
+    """
+    L = load()
+    B = len(As)
+    if B == 0:
+        return []
+    var = _variant(variant)
+    dev = As[0].device
+    Acs = [colmajor(A) for A in As]
+    for A in Acs:
+        _check_input(A)
+    if inplace and any(Ac.data_ptr() != A.data_ptr() for Ac, A in zip(Acs, As)):
+        raise ValueError("inplace=True needs column-major inputs")
+    ms = (ctypes.c_int64 * B)(*[A.shape[0] for A in Acs])
+    ns = (ctypes.c_int64 * B)(*[A.shape[1] for A in Acs])
+    lds = (ctypes.c_int64 * B)(*[_ld(A) for A in Acs])
+    if panel_b is None:
+        panel_b = [0] * B
+    elif isinstance(panel_b, int):
+        panel_b = [panel_b] * B
+    bs = (ctypes.c_int * B)(*[int(b) for b in panel_b])
+    Qs = [A if inplace else empty_colmajor(A.shape[0], A.shape[1], dev) for A in Acs]
+    Rs = [empty_colmajor(A.shape[1], A.shape[1], dev) for A in Acs]
+    # Q_i must share A_i's leading dimension (ldq_i = lda_i)
+    for i, (A, Q) in enumerate(zip(Acs, Qs)):
+        if _ld(Q) != _ld(A):
+            Qs[i] = torch.empty((A.shape[1], _ld(A)), dtype=torch.float64, device=dev).t()[: A.shape[0]]
+    Ap = (ctypes.c_void_p * B)(*[A.data_ptr() for A in Acs])
+    Qp = (ctypes.c_void_p * B)(*[Q.data_ptr() for Q in Qs])
+    Rp = (ctypes.c_void_p * B)(*[R.data_ptr() for R in Rs])
+    ws_bytes = L.cqr_batched_workspace_size(B, ms, ns, bs, var)
+    if ws_bytes == 0:
+        raise CQRError(-2, "cqr_batched_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    if status is None:
+        status = torch.zeros(B, dtype=torch.int32, device=dev)
+    rc = L.cqr_factor_batched(B, ms, ns, lds, bs, Ap, Qp, Rp, var, _ptr(status), _ptr(workspace),
+                              ctypes.c_size_t(workspace.numel()), _stream(stream))
+    if rc != 0:
+        raise CQRError(rc, "cqr_factor_batched")
+    if check:
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        bad = torch.nonzero(status).flatten().tolist()
+        if bad:
+            raise CQRError(int(status[bad[0]].item()), f"cqr_factor_batched (matrix {bad[0]})")
+    return list(zip(Qs, Rs))
+
+
+def probe_fp64_peak(iters: int = 4000) -> float:
+    """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
+    return float(load().cqr_probe_fp64_peak(int(iters)))

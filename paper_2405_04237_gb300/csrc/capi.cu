@@ -1,0 +1,397 @@
+// Host driver and C ABI: the panel loops of mCQR2GS (Alg. 9), CQR2GS
+// (Alg. 6 + Alg. 7), CholeskyQR2 (Alg. 3) and shifted CholeskyQR3 (Alg. 4 +
+// Alg. 5), and the adjoint of A = QR.  Every step is a kernel launch on the
+// caller's stream; nothing here computes on the host, allocates, or waits.
+#include <string.h>
+
+#include "cqr.h"
+#include "cqr_common.cuh"
+
+using namespace cqr;
+
+namespace {
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t status, W, S1, S2, rinv, Z, R1, R2, part, total;
+};
+
+// Workspace plan.  The status word sits at offset 0 (cqr_read_status).
+Layout make_layout(i64 m, i64 n, int b, int variant) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const bool whole = (variant == CQR_CQR2 || variant == CQR_SCQR3);
+  const i64 pw = whole ? n : b;  // panel width of every CQR
+  L.status = take(sizeof(int));
+  L.W = take(sizeof(double) * pw * pw);
+  L.S1 = take(sizeof(double) * pw * pw);
+  L.S2 = take(sizeof(double) * pw * pw);
+  L.rinv = take(sizeof(double) * pw);
+  L.Z = take(variant == CQR_MCQR2GS ? sizeof(double) * n * b : 0);
+  L.R1 = take((variant == CQR_CQR2GS || variant == CQR_SCQR3) ? sizeof(double) * n * n : 0);
+  L.R2 = take((variant == CQR_CQR2GS || variant == CQR_SCQR3) ? sizeof(double) * n * n : 0);
+  size_t pd = tn_partial_doubles(m, (int)pw, (int)pw, 1);
+  if (!whole) {
+    for (i64 j = 0; j * b < n; ++j) {
+      const i64 w = n - (j + 1) * b;  // trailing width after panel j
+      if (w > 0) {
+        size_t d = tn_partial_doubles(m, b, (int)w, 0);
+        if (d > pd) pd = d;
+      }
+      const i64 jb = (j + 1) * b;  // mCQR2GS re-orthogonalisation against jb columns
+      if (variant == CQR_MCQR2GS && jb < n) {
+        size_t d = tn_partial_doubles(m, (int)jb, b, 0);
+        if (d > pd) pd = d;
+      }
+    }
+  }
+  L.part = take(sizeof(double) * pd);
+  L.total = off;
+  return L;
+}
+
+struct Work {
+  int* status;
+  double *W, *S1, *S2, *rinv, *Z, *R1, *R2, *part;
+};
+
+Work bind(void* ws, const Layout& L) {
+  char* p = (char*)ws;
+  Work w;
+  w.status = (int*)(p + L.status);
+  w.W = (double*)(p + L.W);
+  w.S1 = (double*)(p + L.S1);
+  w.S2 = (double*)(p + L.S2);
+  w.rinv = (double*)(p + L.rinv);
+  w.Z = (double*)(p + L.Z);
+  w.R1 = (double*)(p + L.R1);
+  w.R2 = (double*)(p + L.R2);
+  w.part = (double*)(p + L.part);
+  return w;
+}
+
+#define TRY(x)                            \
+  do {                                    \
+    cudaError_t e_ = (x);                 \
+    if (e_ != cudaSuccess) return e_;     \
+  } while (0)
+
+// X := X U^{-1} for any width: 128-column blocks, the coupling between
+// blocks applied as an FMA update in ascending column order (so each element
+// sees the same operation sequence as plain substitution).
+cudaError_t trsm_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
+                     const int* status, cudaStream_t st) {
+  for (int c0 = 0; c0 < b; c0 += kTrsmMaxB) {
+    const int cb = b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB;
+    if (c0 > 0)
+      TRY(nn_product(m, cb, c0, X, ldx, U + (i64)c0 * ldu, ldu, X + (i64)c0 * ldx, ldx, -1.0, 1, 0, 0, status, st));
+    TRY(trsm_rows(m, cb, X + (i64)c0 * ldx, ldx, U + c0 + (i64)c0 * ldu, ldu, rinv + c0, status, st));
+  }
+  return cudaSuccess;
+}
+
+// X := X U^{-T} for any width (adjoint), blocks from the right.
+cudaError_t trsm_t_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
+                       cudaStream_t st) {
+  const int nblk = (b + kTrsmMaxB - 1) / kTrsmMaxB;
+  for (int q = nblk - 1; q >= 0; --q) {
+    const int c0 = q * kTrsmMaxB;
+    const int cb = b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB;
+    const int c1 = c0 + cb;
+    if (c1 < b)  // X[:, c0:c1] -= X[:, c1:b] * (U[c0:c1, c1:b])^T
+      TRY(nn_product_t(m, cb, b - c1, X + (i64)c1 * ldx, ldx, U + c0 + (i64)c1 * ldu, ldu, 1, X + (i64)c0 * ldx,
+                       ldx, -1.0, 1, 0, 0, nullptr, st));
+    TRY(trsm_rows_transposed(m, cb, X + (i64)c0 * ldx, ldx, U + c0 + (i64)c0 * ldu, ldu, rinv + c0, st));
+  }
+  return cudaSuccess;
+}
+
+// Alg. 1 on the m x b panel X (in place): W = X^T X; W = U^T U; X := X U^{-1}.
+cudaError_t cqr_panel(i64 m, int b, double* X, i64 ldx, double* U, i64 ldu, const Work& w, int col0, int shift,
+                      cudaStream_t st) {
+  TRY(tn_product(m, b, b, X, ldx, X, ldx, 1, w.part, w.W, b, w.status, st));
+  TRY(chol_factor(b, w.W, b, U, ldu, w.rinv, col0, w.status, shift, m, st));
+  TRY(trsm_any(m, b, X, ldx, U, ldu, w.rinv, w.status, st));
+  return cudaSuccess;
+}
+
+// Alg. 6 on X (m x n, in place), panels of width b; R (ldr) pre-zeroed.
+cudaError_t cqrgs_run(i64 m, i64 n, int b, double* X, i64 ldx, double* R, i64 ldr, const Work& w, cudaStream_t st) {
+  const i64 k = n / b;
+  for (i64 j = 0; j < k; ++j) {
+    const i64 jb = j * b;
+    double* Xj = X + jb * ldx;
+    TRY(cqr_panel(m, b, Xj, ldx, R + jb + jb * ldr, ldr, w, (int)jb, 0, st));
+    const i64 wd = n - jb - b;
+    if (wd > 0) {
+      double* Yp = R + jb + (jb + b) * ldr;  // Y lands in R_{j,j+1:k}
+      TRY(tn_product(m, b, (int)wd, Xj, ldx, Xj + (i64)b * ldx, ldx, 0, w.part, Yp, ldr, w.status, st));
+      TRY(nn_product(m, (int)wd, b, Xj, ldx, Yp, ldr, Xj + (i64)b * ldx, ldx, -1.0, 1, 0, 0, w.status, st));
+    }
+  }
+  return cudaSuccess;
+}
+
+// Alg. 9 on Q (m x n, in place); R (ldr) pre-zeroed.
+cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w, cudaStream_t st) {
+  const i64 k = n / b;
+  // step 1: [Q_1, R_11] = CQR2(A_1)
+  TRY(cqr_panel(m, b, Q, ldq, w.S1, b, w, 0, 0, st));
+  TRY(cqr_panel(m, b, Q, ldq, w.S2, b, w, 0, 0, st));
+  TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R, ldr, 1.0, 0, 1, 1, w.status, st));
+  for (i64 j = 1; j < k; ++j) {
+    const i64 jb = j * b, wd = n - jb;
+    const double* Qprev = Q + (jb - b) * ldq;
+    double* Aj = Q + jb * ldq;
+    double* Yp = R + (jb - b) + jb * ldr;
+    // steps 3-5: Y = Q_{j-1}^T A_{j:k}; A_{j:k} -= Q_{j-1} Y; R_{j-1,j:k} = Y
+    TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
+    TRY(nn_product(m, (int)wd, b, Qprev, ldq, Yp, ldr, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    // step 6: [P, S1] = CQR(A_j)
+    TRY(cqr_panel(m, b, Aj, ldq, w.S1, b, w, (int)jb, 0, st));
+    // step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z
+    TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
+    TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    // step 8: [Q_j, S2] = CQR(P)
+    TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st));
+    // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
+    TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R + jb + jb * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
+    TRY(nn_product(jb, b, b, w.Z, jb, w.S1, b, R + jb * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t factor_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, int variant, const Work& w,
+                       cudaStream_t st) {
+  switch (variant) {
+    case CQR_MCQR2GS:
+      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st);
+    case CQR_CQR2GS:
+      TRY(cudaMemsetAsync(w.R1, 0, sizeof(double) * n * n, st));
+      TRY(cudaMemsetAsync(w.R2, 0, sizeof(double) * n * n, st));
+      TRY(cqrgs_run(m, n, b, Q, ldq, w.R1, n, w, st));
+      TRY(cqrgs_run(m, n, b, Q, ldq, w.R2, n, w, st));
+      return nn_product(n, (int)n, (int)n, w.R2, n, w.R1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
+    case CQR_CQR2:
+      TRY(cqr_panel(m, (int)n, Q, ldq, w.S1, n, w, 0, 0, st));
+      TRY(cqr_panel(m, (int)n, Q, ldq, w.S2, n, w, 0, 0, st));
+      return nn_product(n, (int)n, (int)n, w.S2, n, w.S1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
+    case CQR_SCQR3:
+      TRY(cqr_panel(m, (int)n, Q, ldq, w.R1, n, w, 0, 1, st));  // Alg. 5 step 1: sCQR
+      TRY(cqr_panel(m, (int)n, Q, ldq, w.S1, n, w, 0, 0, st));  // step 2: CQR2
+      TRY(cqr_panel(m, (int)n, Q, ldq, w.S2, n, w, 0, 0, st));
+      TRY(nn_product(n, (int)n, (int)n, w.S2, n, w.S1, n, w.R2, n, 1.0, 0, 1, 1, w.status, st));
+      return nn_product(n, (int)n, (int)n, w.R2, n, w.R1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+bool overlaps(const double* a, i64 lda, i64 m, i64 n, const double* b, i64 ldb) {
+  const char* a0 = (const char*)a;
+  const char* a1 = (const char*)(a + (n - 1) * lda + m);
+  const char* b0 = (const char*)b;
+  const char* b1 = (const char*)(b + (n - 1) * ldb + m);
+  return a0 < b1 && b0 < a1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cqr_default_panel(int64_t n) {
+  if (n <= 0) return 0;
+  i64 cap = (n + 2) / 3;
+  if (cap > 256) cap = 256;
+  if (cap < 1) cap = 1;
+  for (i64 b = cap; b >= 1; --b)
+    if (n % b == 0) return (int)b;
+  return 1;
+}
+
+static int resolve_panel(int64_t n, int panel_b, int variant) {
+  if (variant == CQR_CQR2 || variant == CQR_SCQR3) return (int)n;
+  return panel_b == 0 ? cqr_default_panel(n) : panel_b;
+}
+
+size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant) {
+  if (m < 1 || n < 1 || m < n || variant < 0 || variant > 3) return 0;
+  const int b = resolve_panel(n, panel_b, variant);
+  if (b < 1 || b > CQR_MAX_PANEL || n % b) return 0;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return 0;
+  return make_layout(m, n, b, variant).total;
+}
+
+int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
+               int64_t ldr, int variant, void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+  if (m < 1 || m < n) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (variant < 0 || variant > 3) return -10;
+  const int b = resolve_panel(n, panel_b, variant);
+  if (panel_b < 0 || b < 1 || b > CQR_MAX_PANEL || n % b) return -5;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return -2;
+  if (!Q) return -6;
+  if (ldq < m || (Q == A && ldq != lda)) return -7;
+  if (Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
+  if (!R) return -8;
+  if (ldr < n) return -9;
+  if (!workspace || ((uintptr_t)workspace & 255)) return -11;
+  const Layout L = make_layout(m, n, b, variant);
+  if (ws_bytes < L.total) return -12;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Work w = bind(workspace, L);
+  cudaGetLastError();  // clear stale errors from earlier, unrelated calls
+  if (cudaMemsetAsync(w.status, 0, sizeof(int), st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (Q != A && cudaMemcpy2DAsync(Q, sizeof(double) * ldq, A, sizeof(double) * lda, sizeof(double) * m, n,
+                                  cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st) != cudaSuccess) return CQR_ERR_CUDA;
+  return 0;
+}
+
+int cqr_read_status(const void* workspace, cqr_stream_t stream, int* status) {
+  if (!workspace || !status) return -1;
+  int h = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&h, workspace, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CQR_ERR_CUDA;
+  *status = h;
+  return 0;
+}
+
+size_t cqr_backward_workspace_size(int64_t m, int64_t n) {
+  if (m < 1 || n < 1 || m < n) return 0;
+  size_t off = 0;
+  off = align256(off + sizeof(double) * n * n);  // G
+  off = align256(off + sizeof(double) * n * n);  // T
+  off = align256(off + sizeof(double) * n * n);  // M
+  off = align256(off + sizeof(double) * n);      // rinv
+  off = align256(off + sizeof(double) * tn_partial_doubles(m, (int)n, (int)n, 0));
+  return off;
+}
+
+int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const double* R, int64_t ldr,
+                 const double* dQ, int64_t lddq, const double* dR, int64_t lddr, double* dA, int64_t ldda,
+                 void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+  if (m < 1 || m < n) return -1;
+  if (n < 1) return -2;
+  if (!Q) return -3;
+  if (ldq < m) return -4;
+  if (!R) return -5;
+  if (ldr < n) return -6;
+  if (dQ && lddq < m) return -8;
+  if (dR && lddr < n) return -10;
+  if (!dA) return -11;
+  if (ldda < m) return -12;
+  if (overlaps(dA, ldda, m, n, Q, ldq) || (dQ && overlaps(dA, ldda, m, n, dQ, lddq))) return -11;
+  if (!workspace || ((uintptr_t)workspace & 255)) return -13;
+  if (ws_bytes < cqr_backward_workspace_size(m, n)) return -14;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* p = (char*)workspace;
+  size_t off = 0;
+  double* G = (double*)(p + off);
+  off = align256(off + sizeof(double) * n * n);
+  double* T = (double*)(p + off);
+  off = align256(off + sizeof(double) * n * n);
+  double* M = (double*)(p + off);
+  off = align256(off + sizeof(double) * n * n);
+  double* rinv = (double*)(p + off);
+  off = align256(off + sizeof(double) * n);
+  double* part = (double*)(p + off);
+  cudaGetLastError();
+  const int nn = (int)n;
+  // G = Qbar^T Q
+  if (dQ) {
+    if (tn_product(m, nn, nn, dQ, lddq, Q, ldq, 0, part, G, n, nullptr, st) != cudaSuccess) return CQR_ERR_CUDA;
+  } else if (cudaMemsetAsync(G, 0, sizeof(double) * n * n, st) != cudaSuccess) {
+    return CQR_ERR_CUDA;
+  }
+  // T = R Rbar^T (R upper: k >= row)
+  if (dR) {
+    if (nn_product_t(n, nn, nn, R, ldr, dR, lddr, 1, T, n, 1.0, 0, 1, 0, nullptr, st) != cudaSuccess)
+      return CQR_ERR_CUDA;
+  } else if (cudaMemsetAsync(T, 0, sizeof(double) * n * n, st) != cudaSuccess) {
+    return CQR_ERR_CUDA;
+  }
+  if (backward_middle(nn, T, G, M, st) != cudaSuccess) return CQR_ERR_CUDA;
+  // B = Qbar + Q M  (into dA)
+  if (dQ) {
+    if (cudaMemcpy2DAsync(dA, sizeof(double) * ldda, dQ, sizeof(double) * lddq, sizeof(double) * m, n,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return CQR_ERR_CUDA;
+  }
+  if (nn_product(m, nn, nn, Q, ldq, M, n, dA, ldda, 1.0, dQ ? 1 : 0, 0, 0, nullptr, st) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  // Abar = B R^{-T}
+  if (diag_reciprocal(nn, R, ldr, rinv, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (trsm_t_any(m, nn, dA, ldda, R, ldr, rinv, st) != cudaSuccess) return CQR_ERR_CUDA;
+  return 0;
+}
+
+size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant) {
+  if (batch < 0 || (variant != CQR_MCQR2GS && variant != CQR_CQR2GS)) return 0;
+  if (batch > 0 && (!m || !n || !panel_b)) return 0;
+  size_t mx = 256;
+  for (int i = 0; i < batch; ++i) {
+    const size_t s = cqr_workspace_size(m[i], n[i], panel_b[i], variant);
+    if (s == 0) return 0;
+    if (s > mx) mx = s;
+  }
+  return mx;
+}
+
+int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* lda, const int* panel_b,
+                       double* const* A, double* const* Q, double* const* R, int variant, int* status,
+                       void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+  if (batch < 0) return -1;
+  if (batch == 0) return 0;
+  if (!m || !n || !lda || !panel_b) return -2;
+  if (!A || !Q || !R) return -6;
+  if (variant != CQR_MCQR2GS && variant != CQR_CQR2GS) return -9;
+  if (!status) return -10;
+  if (!workspace || ((uintptr_t)workspace & 255)) return -11;
+  if (ws_bytes < cqr_batched_workspace_size(batch, m, n, panel_b, variant)) return -12;
+  for (int i = 0; i < batch; ++i) {
+    if (m[i] < 1 || n[i] < 1 || m[i] < n[i] || lda[i] < m[i]) return -2;
+    const int b = resolve_panel(n[i], panel_b[i], variant);
+    if (panel_b[i] < 0 || b < 1 || b > CQR_MAX_PANEL || n[i] % b) return -5;
+    if (!A[i] || !Q[i] || !R[i]) return -6;
+    if (Q[i] != A[i] && overlaps(A[i], lda[i], m[i], n[i], Q[i], lda[i])) return -7;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaGetLastError();
+  if (cudaMemsetAsync(status, 0, sizeof(int) * batch, st) != cudaSuccess) return CQR_ERR_CUDA;
+  for (int i = 0; i < batch; ++i) {
+    const int b = resolve_panel(n[i], panel_b[i], variant);
+    const Layout L = make_layout(m[i], n[i], b, variant);
+    Work w = bind(workspace, L);
+    w.status = status + i;
+    if (Q[i] != A[i] && cudaMemcpy2DAsync(Q[i], sizeof(double) * lda[i], A[i], sizeof(double) * lda[i],
+                                          sizeof(double) * m[i], n[i], cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return CQR_ERR_CUDA;
+    if (cudaMemsetAsync(R[i], 0, sizeof(double) * n[i] * n[i], st) != cudaSuccess) return CQR_ERR_CUDA;
+    if (factor_run(m[i], n[i], b, Q[i], lda[i], R[i], n[i], variant, w, st) != cudaSuccess) return CQR_ERR_CUDA;
+  }
+  return 0;
+}
+
+const char* cqr_status_string(int status) {
+  if (status == 0) return "success";
+  if (status == CQR_ERR_CUDA) return "a CUDA launch or copy failed";
+  if (status == CQR_STATUS_TIMEOUT) return "a bounded wait in the batched persistent kernel expired";
+  if (status > 0) return "Cholesky breakdown: the Gram matrix is not numerically positive definite (status = column + 1)";
+  return "invalid argument (status = -(argument position))";
+}
+
+double cqr_probe_fp64_peak(int iters) { return probe_fp64(iters > 0 ? iters : 4000); }
+
+}  // extern "C"

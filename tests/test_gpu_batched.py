@@ -1,0 +1,58 @@
+"""Batched factorisation: every member equals the single-call result bit for
+bit (same sizes, same panel width, same deterministic reduction order), and
+matches the oracle within the parity tolerances."""
+import numpy as np
+import pytest
+
+from _helpers import orth_err, rel_diff, resid
+from testmatrices import batch_specs, make_test_matrix
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _t(x):
+    return torch.from_numpy(np.asfortranarray(x)).cuda()
+
+
+def _panel_for(n, kappa):
+    # enough panels for the condition number (3 at 1e15, Sec. 5.4)
+    k = 1 if kappa < 1e7 else (2 if kappa < 1e11 else 4)
+    while n % k:
+        k += 1
+    return n // k
+
+
+@pytest.mark.parametrize("variant", ["mcqr2gs", "cqr2gs"])
+def test_batched_equals_single(cuda_lib, oracle, variant):
+    P = cuda_lib
+    specs = batch_specs(count=24, m_range=(200, 30000))
+    As = [make_test_matrix(m, n, k, s) for (m, n, k, s) in specs]
+    bs = [_panel_for(n, k) for (m, n, k, s) in specs]
+    if variant == "cqr2gs":  # CQR2GS needs narrower panels at high kappa (Sec. 5.3)
+        bs = [max(1, n // 8) if k > 1e7 else b for b, (m, n, k, s) in zip(bs, specs)]
+    res = P.factor_batched([_t(A) for A in As], bs, variant)
+    for i, ((Qb, Rb), A, b, spec) in enumerate(zip(res, As, bs, specs)):
+        Qs, Rs = P.factor(_t(A), b, variant)
+        assert torch.equal(Qb, Qs) and torch.equal(Rb, Rs), i
+        Qn, Rn = Qb.cpu().numpy(), Rb.cpu().numpy()
+        assert orth_err(Qn) < 1e-13 and resid(A, Qn, Rn) < 1e-14, (i, spec)
+        if spec[2] <= 1e6:
+            Qo, Ro = (oracle.mcqr2gs if variant == "mcqr2gs" else oracle.cqr2gs)(A, b)
+            assert rel_diff(Rn, Ro) < 1e-11
+
+
+def test_batched_status_per_matrix(cuda_lib):
+    P = cuda_lib
+    A1 = make_test_matrix(3000, 16, 1e2, seed=2100)
+    A2 = make_test_matrix(4000, 16, 1e2, seed=2101)
+    A2[:, 7] = 0.0
+    A3 = make_test_matrix(5000, 32, 1e2, seed=2102)
+    status = torch.zeros(3, dtype=torch.int32, device="cuda")
+    P.factor_batched([_t(A1), _t(A2), _t(A3)], [4, 4, 8], check=False, status=status)
+    torch.cuda.synchronize()
+    assert status.tolist() == [0, 8, 0]
+
+
+def test_batched_empty(cuda_lib):
+    assert cuda_lib.factor_batched([]) == []
