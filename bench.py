@@ -1,0 +1,477 @@
+#!/usr/bin/env python
+"""Benchmark: mCQR2GS FP64 TFLOP/s on one GB300 (plus batched and adjoint).
+
+One step = one mCQR2GS factorisation (Alg. 9) of the m = 2^23, n = 1024,
+kappa = 1e15 test matrix A = U diag(sigma) V^T (Sec. 2.2 construction,
+seeded, synthetic), out of place (A is read, Q and R are written), panel
+width chosen by the autotuner among {64, 128, 256}.  Rate = 4 m n^2 / t,
+the paper's flop convention for mCQR2GS (Table 2 with the final R product
+removed, Sec. 5.4).  The matrix (68.7 GB) is far larger than L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle on the host cores (a bounded row
+sample of the same workload) and prints the same JSON line with
+"impl": "reference".  With --gpus N > 1 (under torchrun) every rank factors
+its own replica (replicas only: the library has no multi-GPU path) and the
+value is the sum over ranks of the work divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mCQR2GS FP64 TFLOP/s; batched QR/s vs looped; at ‖I−QᵀQ‖_F≤1e-13"
+M_FULL, N_FULL, KAPPA_FULL, SEED_FULL = 1 << 23, 1024, 1e15, 1002
+PANEL_CANDIDATES = (64, 128, 256)
+N_SM = 152
+FP64_FLOP_PER_CLK_SM = 4       # 2 DFMA per clock per SM (measured)
+SM_MAX_MHZ = 2070.0            # GB300 maximum SM clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=M_FULL)
+    p.add_argument("--n", type=int, default=N_FULL)
+    p.add_argument("--kappa", type=float, default=KAPPA_FULL)
+    p.add_argument("--panel", type=int, default=0, help="0 = autotune among 64/128/256")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint sub-benchmarks")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-check", action="store_true", help="skip the accuracy norms")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- distributed plumbing
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def allreduce_max(dist, x):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(dist, x):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+def oracle_sample(n, b, kappa, target_s):
+    """A row sample of the workload (same n, b, kappa construction) sized so
+    that one oracle mCQR2GS on it takes about target_s seconds."""
+    import oracle
+    from testmatrices import make_test_matrix
+
+    oracle.build()
+    m_s = 1 << 12
+    A = make_test_matrix(m_s, n, kappa, seed=SEED_FULL)
+    t0 = time.perf_counter()
+    oracle.mcqr2gs(A, b, check=False)
+    dt = time.perf_counter() - t0
+    while dt * 2 <= target_s and m_s < (1 << 18):
+        m_s *= 2
+        dt *= 2
+    if A.shape[0] != m_s:
+        A = make_test_matrix(m_s, n, kappa, seed=SEED_FULL)
+    return A
+
+
+def time_oracle(A, b):
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.mcqr2gs(A, b, check=False)
+    dt = time.perf_counter() - t0
+    m_s, n = A.shape
+    return 4.0 * m_s * n * n / dt / 1e12, dt
+
+
+def cpu_baseline(n, b, kappa, target_s=20.0):
+    """The oracle timed on the host cores on a bounded row sample."""
+    import oracle
+
+    A = oracle_sample(n, b, kappa, target_s)
+    v, dt = time_oracle(A, b)
+    desc = (f"oracle mCQR2GS (Alg. 9, plain C, OpenMP) on a {A.shape[0]} x {n} row sample of the same "
+            f"construction (kappa={kappa:.0e}, b={b}), one run of {dt:.1f} s")
+    return v, desc, oracle.num_threads(), dt, A.shape[0]
+
+
+def run_reference(args, dist, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    b = args.panel or 128
+    A = oracle_sample(args.n, b, args.kappa, target_s=8.0)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        v, dt = time_oracle(A, b)
+        if i >= args.warmup:
+            steps.append((v, dt))
+    v = statistics.median(x[0] for x in steps)
+    m_s = A.shape[0]
+    desc = (f"oracle mCQR2GS (Alg. 9, plain C, OpenMP) on a {m_s} x {args.n} row sample of the workload "
+            f"(kappa={args.kappa:.0e}, b={b}); rate scaled by the flop count 4 m n^2 of the sample")
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": v,
+        "unit": "TFLOP/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(x[1] for x in steps),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"mCQR2GS m={args.m} n={args.n} kappa={args.kappa:.0e}", "m": args.m, "n": args.n,
+                   "kappa": args.kappa, "panel_b": b, "sample_rows": m_s},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def accuracy(A, Q, R, chunk=1 << 20):
+    """||I - Q^T Q||_F, ||A - Q R||_F / ||A||_F with torch FP64 GEMMs (row chunks)."""
+    import torch
+
+    m, n = Q.shape
+    G = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    rs2 = torch.zeros((), dtype=torch.float64, device="cuda")
+    a2 = torch.zeros((), dtype=torch.float64, device="cuda")
+    for r0 in range(0, m, chunk):
+        r1 = min(m, r0 + chunk)
+        Qc = Q[r0:r1]
+        G += Qc.t() @ Qc
+        D = A[r0:r1] - Qc @ R
+        rs2 += (D * D).sum()
+        a2 += (A[r0:r1] * A[r0:r1]).sum()
+    orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - G).item()
+    return orth, (rs2.sqrt() / a2.sqrt()).item()
+
+
+def bench_batched(P):
+    """Batched workload: 512 matrices, m in [2000, 200000], n in {16..128},
+    kappa log-uniform in [1e2, 1e15]; one batched call vs a loop of single
+    calls, matrices per second."""
+    import torch
+
+    from testmatrices import batch_specs, make_test_matrix_cuda
+
+    specs = batch_specs(512)
+
+    def panel(n, k):
+        kk = 1 if k < 1e7 else (2 if k < 1e11 else 3)
+        while n % kk:
+            kk += 1
+        return n // kk
+
+    As, bs = [], []
+    for (m, n, k, s) in specs:
+        As.append(make_test_matrix_cuda(m, n, k, s, chunk_rows=1 << 18))
+        bs.append(panel(n, k))
+    torch.cuda.synchronize()
+    flops = sum(4.0 * A.shape[0] * A.shape[1] ** 2 for A in As)
+    # batched
+    P.factor_batched(As, bs)  # warm-up with status check
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.factor_batched(As, bs, check=False)
+    e1.record()
+    e1.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    # looped single calls (workspaces allocated up front)
+    Qs = [P.empty_colmajor(A.shape[0], A.shape[1], "cuda") for A in As]
+    Rs = [P.empty_colmajor(A.shape[1], A.shape[1], "cuda") for A in As]
+    wss = [torch.empty(P.workspace_size(A.shape[0], A.shape[1], b), dtype=torch.uint8, device="cuda")
+           for A, b in zip(As, bs)]
+    for A, b, Q, R, ws in zip(As, bs, Qs, Rs, wss):
+        P.factor(A, b, out=(Q, R), workspace=ws, check=False)
+    torch.cuda.synchronize()
+    e0.record()
+    for A, b, Q, R, ws in zip(As, bs, Qs, Rs, wss):
+        P.factor(A, b, out=(Q, R), workspace=ws, check=False)
+    e1.record()
+    e1.synchronize()
+    tl = e0.elapsed_time(e1) / 1e3
+    return {"matrices": len(As), "batched_qr_per_s": len(As) / tb, "looped_qr_per_s": len(As) / tl,
+            "speedup": tl / tb, "batched_tflops": flops / tb / 1e12, "looped_tflops": flops / tl / 1e12,
+            "workload": "512 matrices, m U[2000,200000], n in {16,32,64,128}, kappa log-U[1e2,1e15]"}
+
+
+def bench_adjoint(P):
+    """Forward + hand-written adjoint at m = 2^20, n = 128, kappa = 1e8."""
+    import torch
+
+    from testmatrices import make_test_matrix_cuda
+
+    m, n = 1 << 20, 128
+    A = make_test_matrix_cuda(m, n, 1e8, 1004)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1005)
+    dQ = torch.randn((n, m), generator=g, dtype=torch.float64, device="cuda").t()
+    dR = torch.triu(torch.randn((n, n), generator=g, dtype=torch.float64, device="cuda"))
+    b = 64
+    Q, R = P.factor(A, b)
+    P.backward(Q, R, dQ, dR)
+    torch.cuda.synchronize()
+    tf, tb = [], []
+    for _ in range(3):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        Q, R = P.factor(A, b, check=False)
+        e1.record()
+        P.backward(Q, R, dQ, dR)
+        e2.record()
+        e2.synchronize()
+        tf.append(e0.elapsed_time(e1))
+        tb.append(e1.elapsed_time(e2))
+    f, bw = min(tf), min(tb)
+    return {"m": m, "n": n, "panel_b": b, "forward_ms": f, "backward_ms": bw, "backward_over_forward": bw / f,
+            "forward_tflops": 4.0 * m * n * n / f / 1e9, "backward_tflops": 5.0 * m * n * n / bw / 1e9}
+
+
+def run_ours(args, dist, rank, world):
+    import torch
+
+    import paper_2405_04237_gb300 as P
+    from paper_2405_04237_gb300.autotune import autotune
+    from testmatrices import make_test_matrix_cuda
+
+    P.load()
+    dev = torch.cuda.current_device()
+    m, n, kappa = args.m, args.n, args.kappa
+    probe = P.probe_fp64_peak(20000)
+    b = args.panel or autotune(m, n, "mcqr2gs", kappa, cands=[c for c in PANEL_CANDIDATES if n % c == 0 and n // c >= 3])
+    A = make_test_matrix_cuda(m, n, kappa, SEED_FULL + 100 * rank)
+    Q = P.empty_colmajor(m, n, "cuda")
+    R = P.empty_colmajor(n, n, "cuda")
+    ws = torch.empty(P.workspace_size(m, n, b, "mcqr2gs"), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    for i in range(args.warmup):
+        P.factor(A, b, out=(Q, R), workspace=ws, check=(i == 0))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    barrier(dist)
+    torch.cuda.synchronize()
+    l0 = P.launch_count()
+    with ClockSampler(dev) as clk, P.KernelTimer(100000) as kt:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            P.factor(A, b, out=(Q, R), workspace=ws, check=False, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = P.launch_count() - l0
+    t_step = e0.elapsed_time(e1) / 1e3 / args.steps
+    status = P.read_status(ws)
+    t_max = allreduce_max(dist, t_step)
+    launches_all = int(allreduce_sum(dist, launches))
+    flops = 4.0 * m * n * n
+    value = world * flops / t_max / 1e12
+    prof = kt.read()
+    clocks = clk.summary()
+
+    # dominant kernel (largest device time) and its roofline
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    tot_ms = sum(v["ms"] for v in prof.values())
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    ach = prof[dom]["flops"] / (prof[dom]["ms"] * 1e-3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": dom,
+                "peak_note": "FP64 FMA pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); "
+                             f"DFMA microbenchmark in this run: {probe / 1e3:.4f} TFLOP/s",
+                "share_of_device_time": prof[dom]["ms"] / tot_ms if tot_ms else None,
+                "launches": prof[dom]["launches"]}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "share": v["ms"] / tot_ms if tot_ms else None,
+                   "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None}
+               for k, v in prof.items() if v["launches"]}
+
+    acc = {}
+    if not args.no_check:
+        orth, res = accuracy(A, Q, R)
+        acc = {"orth_fro": orth, "orth_fro_over_sqrt_n": orth / n ** 0.5, "resid_rel": res, "status": status}
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        Ah.copy_(A)
+        Ad = A  # device input buffer, refilled from the host every step
+        barrier(dist)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            Ad.copy_(Ah, non_blocking=True)
+            P.factor(Ad, b, out=(Q, R), workspace=ws, check=False, stream=stream)
+            Qh.copy_(Q, non_blocking=True)
+            Rh.copy_(R, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e = allreduce_max(dist, e0.elapsed_time(e1) / 1e3 / args.steps)
+        e2e = {"value": world * flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * m * n,
+               "d2h_bytes_per_step": 8 * (m * n + n * n), "ms_per_step": 1e3 * t_e2e}
+        del Ah, Qh, Rh
+
+    extras = {}
+    del A, Q, R, ws
+    torch.cuda.empty_cache()
+    if not args.no_extras and rank == 0:
+        extras["batched"] = bench_batched(P)
+        torch.cuda.empty_cache()
+        extras["adjoint"] = bench_adjoint(P)
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        v, desc, threads, dt, m_s = cpu_baseline(n, b, kappa)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "TFLOP/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_max,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"mCQR2GS m={m} n={n} kappa={kappa:.0e} b={b} (out of place)", "m": m, "n": n,
+                       "kappa": kappa, "panel_b": b, "variant": "mcqr2gs",
+                       "l2": f"inputs larger than L2 ({8 * m * n / 1e9:.1f} GB), no flush",
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_all,
+            "clocks": clocks,
+            "accuracy": acc,
+            "kernels": kernels,
+            "fp64_probe_tflops": probe / 1e3,
+            **extras,
+        }
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    dist, rank, world = dist_init(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist, rank, world)
+        else:
+            run_ours(args, dist, rank, world)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,34 @@ const char* cqr_status_string(int status);
  */
 double cqr_probe_fp64_peak(int iters);
 
+/*
+ * Launch accounting and kernel timing (measurement support; not in the
+ * paper).  Kernel classes: 0 Gram (syrk partials), 1 projection (split-m
+ * X^T Z partials), 2 split-m reduction, 3 Cholesky, 4 triangular solve,
+ * 5 GEMM update (A -= Q Y, P -= Q Z, R products), 6 adjoint helpers and
+ * probes, 7 batched scheduler.
+ *
+ * cqr_launch_count: number of kernels this process has launched through the
+ *   library so far (host counter; monotonic).
+ * cqr_profile_enable: from now on, bracket every launch with a CUDA event
+ *   pair on its stream (host-side event objects, created up front for
+ *   `capacity` launches; later launches are not timed).  Clears earlier
+ *   records.  Do not enable around a CUDA-graph capture.  Returns 0, -1 for
+ *   capacity < 1, CQR_ERR_CUDA if events cannot be created.
+ * cqr_profile_disable: stop recording (records are kept).
+ * cqr_profile_read: synchronises on the recorded events and returns, for
+ *   kernel class `cls`, the number of timed launches, their summed device
+ *   time in ms, and their summed algorithmic FLOP counts (Gram m b (b+1),
+ *   projection 2 m p q, Cholesky b^3/3, triangular solve m b^2, update
+ *   2 M N K).  Returns 0, -1 for a bad argument, CQR_ERR_CUDA on error.
+ * cqr_kernel_class_name: static name of a kernel class.
+ */
+unsigned long long cqr_launch_count(void);
+int cqr_profile_enable(int capacity);
+int cqr_profile_disable(void);
+int cqr_profile_read(int cls, long long* launches, double* total_ms, double* flops);
+const char* cqr_kernel_class_name(int cls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ from ._capi import CQRError, VARIANTS, load, status_string
 __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
     "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "colmajor", "empty_colmajor",
+    "launch_count", "KernelTimer",
 ]
 
 
@@ -221,3 +222,38 @@ def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, s
 def probe_fp64_peak(iters: int = 4000) -> float:
     """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
     return float(load().cqr_probe_fp64_peak(int(iters)))
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().cqr_launch_count())
+
+
+class KernelTimer:
+    """Context manager: times every library kernel launch inside it with CUDA
+    events on its own stream; ``.read()`` gives per-class launches, device ms
+    and algorithmic FLOPs."""
+
+    def __init__(self, capacity: int = 100000):
+        self.capacity = int(capacity)
+
+    def __enter__(self):
+        rc = load().cqr_profile_enable(self.capacity)
+        if rc != 0:
+            raise CQRError(rc, "cqr_profile_enable")
+        return self
+
+    def __exit__(self, *exc):
+        load().cqr_profile_disable()
+        return False
+
+    def read(self) -> dict:
+        out = {}
+        L = load()
+        for cls, name in enumerate(_capi.KERNEL_CLASSES):
+            n, ms, fl = ctypes.c_longlong(0), ctypes.c_double(0), ctypes.c_double(0)
+            rc = L.cqr_profile_read(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl))
+            if rc != 0:
+                raise CQRError(rc, "cqr_profile_read")
+            out[name] = {"launches": int(n.value), "ms": float(ms.value), "flops": float(fl.value)}
+        return out

@@ -24,7 +24,10 @@ EXPORTS = [
     "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status",
     "cqr_backward_workspace_size", "cqr_backward", "cqr_batched_workspace_size",
     "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak",
+    "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
 ]
+KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "adjoint_misc",
+                  "batched"]
 
 
 class CQRError(RuntimeError):
@@ -66,6 +69,12 @@ def load(build_if_missing: bool = True):
             "cqr_factor_batched": (c_int, [c_int, P64, P64, P64, PI, PV, PV, PV, c_int, vp, vp, sz, vp]),
             "cqr_status_string": (ctypes.c_char_p, [c_int]),
             "cqr_probe_fp64_peak": (ctypes.c_double, [c_int]),
+            "cqr_launch_count": (ctypes.c_ulonglong, []),
+            "cqr_profile_enable": (c_int, [c_int]),
+            "cqr_profile_disable": (c_int, []),
+            "cqr_profile_read": (c_int, [c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
+            "cqr_kernel_class_name": (ctypes.c_char_p, [c_int]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)

@@ -88,4 +88,21 @@ cudaError_t diag_reciprocal(int n, const double* R, i64 ldr, double* rinv, cudaS
 // FP64 FMA throughput probe (GFLOP/s).
 double probe_fp64(int iters);
 
+// ---------------------------------------------------------------------------
+// Launch accounting (prof.cu).  Every launch is wrapped in prof_begin /
+// prof_end with its kernel class and algorithmic FLOP count.
+enum KernelClass {
+  kGram = 0,       // syrk partials of W = X^T X
+  kProjection = 1, // split-m partials of Y = X^T Z
+  kReduce = 2,     // fixed-order sums of split-m partials
+  kCholesky = 3,
+  kTrsm = 4,
+  kUpdate = 5,     // C = beta C + alpha A B (GS / re-orthogonalisation updates, R products)
+  kMisc = 6,
+  kBatched = 7,
+  kNumClasses = 8
+};
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, double flops, cudaStream_t st);
+
 }  // namespace cqr

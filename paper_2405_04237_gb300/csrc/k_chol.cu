@@ -144,22 +144,30 @@ cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* r
                            (int)(sizeof(double) * (2 * 128 + 128 * 128)));
       attr = true;
     }
+    prof_begin(kCholesky, st);
     chol_kernel<true><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m);
+    prof_end(kCholesky, (double)b * b * b / 3.0, st);
   } else {
     const size_t smem = sizeof(double) * (size_t)2 * b;
+    prof_begin(kCholesky, st);
     chol_kernel<false><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m);
+    prof_end(kCholesky, (double)b * b * b / 3.0, st);
   }
   return cudaGetLastError();
 }
 
 cudaError_t backward_middle(int n, const double* T, const double* G, double* M, cudaStream_t st) {
   const int thr = 256;
+  prof_begin(kMisc, st);
   backward_middle_kernel<<<(n * n + thr - 1) / thr, thr, 0, st>>>(n, T, G, M);
+  prof_end(kMisc, (double)n * n, st);
   return cudaGetLastError();
 }
 
 cudaError_t diag_reciprocal(int n, const double* R, i64 ldr, double* rinv, cudaStream_t st) {
+  prof_begin(kMisc, st);
   diag_reciprocal_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, R, ldr, rinv);
+  prof_end(kMisc, (double)n, st);
   return cudaGetLastError();
 }
 
@@ -171,18 +179,30 @@ double probe_fp64(int iters) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int blocks = sms * 4, threads = 256;
-  probe_kernel<<<blocks, threads>>>(iters / 10 + 1, 0.999999, 1e-7);  // warm-up
-  cudaEventRecord(e0);
-  probe_kernel<<<blocks, threads>>>(iters, 0.999999, 1e-7);
-  cudaEventRecord(e1);
-  cudaError_t err = cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
+  // warm-up long enough for the clocks to settle, then the best of three
+  for (int w = 0; w < 3; ++w) {
+    prof_begin(kMisc, 0);
+    probe_kernel<<<blocks, threads>>>(iters, 0.999999, 1e-7);
+    prof_end(kMisc, 0.0, 0);
+  }
+  float best = 0.f;
+  cudaError_t err = cudaSuccess;
+  for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+    cudaEventRecord(e0);
+    prof_begin(kMisc, 0);
+    probe_kernel<<<blocks, threads>>>(iters, 0.999999, 1e-7);
+    prof_end(kMisc, 0.0, 0);
+    cudaEventRecord(e1);
+    err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms > 0.f && (best == 0.f || ms < best)) best = ms;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (err != cudaSuccess || ms <= 0.f) return -1.0;
+  if (err != cudaSuccess || best <= 0.f) return -1.0;
   const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
-  return flops / (ms * 1e-3) / 1e9;
+  return flops / (best * 1e-3) / 1e9;
 }
 
 }  // namespace cqr

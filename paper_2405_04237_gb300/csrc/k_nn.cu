@@ -169,12 +169,14 @@ cudaError_t nn_product_t(i64 M, int N, int K, const double* A, i64 lda, const do
   int TM = 4096 / TN;
   a.tiles_n = (N + TN - 1) / TN;
   const i64 blocks = ((M + TM - 1) / TM) * a.tiles_n;
+  prof_begin(kUpdate, st);
   switch (TN) {
     case 8: launch_nn<512, 8>(a, neg, blocks, st); break;
     case 16: launch_nn<256, 16>(a, neg, blocks, st); break;
     case 32: launch_nn<128, 32>(a, neg, blocks, st); break;
     default: launch_nn<64, 64>(a, neg, blocks, st); break;
   }
+  prof_end(kUpdate, 2.0 * (double)M * N * K, st);
   return cudaGetLastError();
 }
 

@@ -449,15 +449,17 @@ cudaError_t tn_product(i64 m, int p, int q, const double* X, i64 ldx, const doub
     a.P = P.S;
     a.part = part;
     a.status = status;
-    if (m > 0) syrk_partial_kernel<<<P.S, s.threads, s.smem, st>>>(a);
+    if (m > 0) {
+      prof_begin(kGram, st);
+      syrk_partial_kernel<<<P.S, s.threads, s.smem, st>>>(a);
+      prof_end(kGram, (double)m * p * (p + 1), st);
+    }
     const int thr = 256;
     const int blocks = (p * p + thr - 1) / thr;
-    if (m > 0) {
-      syrk_reduce_kernel<<<blocks, thr, 0, st>>>(part, p, P.S, C, ldc, status);
-    } else {
-      // empty sum: W = 0 (handled by a reduce over zero partials)
-      syrk_reduce_kernel<<<blocks, thr, 0, st>>>(part, p, 0, C, ldc, status);
-    }
+    const i64 nsum = m > 0 ? P.S : 0;  // m == 0: the empty sum, W = 0
+    prof_begin(kReduce, st);
+    syrk_reduce_kernel<<<blocks, thr, 0, st>>>(part, p, nsum, C, ldc, status);
+    prof_end(kReduce, (double)nsum * p * (p + 1) / 2, st);
     return cudaGetLastError();
   }
   TnArgs a;
@@ -476,18 +478,22 @@ cudaError_t tn_product(i64 m, int p, int q, const double* X, i64 ldx, const doub
   a.status = status;
   if (m > 0) {
     dim3 grid((unsigned)P.S);
+    prof_begin(kProjection, st);
     switch (P.tp) {
       case 8: launch_tn_q<8>(P.tq, grid, st, a); break;
       case 16: launch_tn_q<16>(P.tq, grid, st, a); break;
       case 32: launch_tn_q<32>(P.tq, grid, st, a); break;
       default: launch_tn_q<64>(P.tq, grid, st, a); break;
     }
+    prof_end(kProjection, 2.0 * (double)m * p * q, st);
   }
   const i64 pq = (i64)p * q;
   const int thr = 256;
   const unsigned blocks = (unsigned)((pq + thr - 1) / thr);
+  prof_begin(kReduce, st);
   tn_reduce_kernel<<<blocks, thr, 0, st>>>(part, p, q, P.tp, P.tq, P.tiles_p, a.nb, m > 0 ? a.T : 0,
                                            m > 0 ? a.P : 1, C, ldc, status);
+  prof_end(kReduce, m > 0 ? (double)(P.S + P.ntiles) / P.ntiles * pq : 0.0, st);
   return cudaGetLastError();
 }
 

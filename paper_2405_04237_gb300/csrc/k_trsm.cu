@@ -153,7 +153,9 @@ cudaError_t trsm_rows(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu
   if (b > kTrsmMaxB) return cudaErrorInvalidValue;
   set_trsm_attr();
   const i64 blocks = (m + kRows - 1) / kRows;
+  prof_begin(kTrsm, st);
   trsm_rows_kernel<<<(unsigned)blocks, kRows, trsm_smem(b), st>>>(m, b, X, ldx, U, ldu, rinv, status);
+  prof_end(kTrsm, (double)m * b * b, st);
   return cudaGetLastError();
 }
 
@@ -163,7 +165,9 @@ cudaError_t trsm_rows_transposed(i64 m, int b, double* X, i64 ldx, const double*
   if (b > kTrsmMaxB) return cudaErrorInvalidValue;
   set_trsm_attr();
   const i64 blocks = (m + kRows - 1) / kRows;
+  prof_begin(kTrsm, st);
   trsm_rows_t_kernel<<<(unsigned)blocks, kRows, trsm_smem(b), st>>>(m, b, X, ldx, U, ldu, rinv);
+  prof_end(kTrsm, (double)m * b * b, st);
   return cudaGetLastError();
 }
 
