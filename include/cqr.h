@@ -131,9 +131,10 @@ int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const doubl
 size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant);
 
 /*
- * cqr_factor_batched: factors `batch` independent matrices A_i = Q_i R_i in
- * one persistent launch sequence (Alg. 9 per matrix; variant must be
- * CQR_MCQR2GS or CQR_CQR2GS).
+ * cqr_factor_batched: factors `batch` independent matrices A_i = Q_i R_i
+ * (variant CQR_MCQR2GS or CQR_CQR2GS).  Not in the paper (batching of many
+ * small problems); each matrix follows Alg. 9 / Alg. 7 exactly as
+ * cqr_factor() does.
  *   batch                  number of matrices, >= 0                  (arg 1)
  *   m, n, lda, panel_b     HOST arrays of length batch                (args 2-5)
  *   A, Q, R                HOST arrays of DEVICE pointers; ldq_i = lda_i
@@ -143,10 +144,14 @@ size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n,
  *                          status codes as in cqr_factor              (arg 10)
  *   workspace, ws_bytes    >= cqr_batched_workspace_size()            (args 11, 12)
  *   stream                 CUDA stream                               (arg 13)
- * The descriptor table is copied to the workspace with one host-to-device
- * copy per call, so for CUDA-graph replay the pointer arrays must be stable.
- * Each matrix's result is identical (bitwise) to a cqr_factor() call with
- * the same sizes and panel width.
+ * The matrices are distributed (largest work first) over a pool of
+ * library-owned streams that are forked from `stream` and joined back into
+ * it with events, so small grids, Cholesky islands and reductions of
+ * different matrices overlap; the whole call is ordered on `stream`, reads
+ * no host memory after it returns, and can be captured into a CUDA graph.
+ * Each matrix's result is bitwise identical to a cqr_factor() call with the
+ * same sizes and panel width.  Calls that share the workspace must not
+ * overlap on the GPU.
  */
 int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* lda, const int* panel_b,
                        double* const* A, double* const* Q, double* const* R, int variant, int* status,

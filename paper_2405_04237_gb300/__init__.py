@@ -25,7 +25,7 @@ from ._capi import CQRError, VARIANTS, load, status_string
 __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
     "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "colmajor", "empty_colmajor",
-    "launch_count", "KernelTimer",
+    "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size",
 ]
 
 
@@ -76,6 +76,12 @@ def default_panel(n: int) -> int:
 
 def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs") -> int:
     return int(load().cqr_workspace_size(int(m), int(n), int(panel_b), _variant(variant)))
+
+
+def batched_workspace_size(ms, ns, panel_b, variant="mcqr2gs") -> int:
+    B = len(ms)
+    return int(load().cqr_batched_workspace_size(B, (ctypes.c_int64 * B)(*ms), (ctypes.c_int64 * B)(*ns),
+                                                 (ctypes.c_int * B)(*[int(b) for b in panel_b]), _variant(variant)))
 
 
 def read_status(workspace: torch.Tensor, stream=None) -> int:
@@ -217,6 +223,61 @@ def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, s
         if bad:
             raise CQRError(int(status[bad[0]].item()), f"cqr_factor_batched (matrix {bad[0]})")
     return list(zip(Qs, Rs))
+
+
+class BatchedGraph:
+    """A batched factorisation captured once into a CUDA graph and replayed.
+
+    Inputs are the given column-major matrices (their storage is read on every
+    replay, so refill them in place to factor new data); outputs Q_i, R_i and
+    the per-matrix status live in buffers owned by this object.  The first
+    (eager) call checks every status; capture happens after it.
+    """
+
+    def __init__(self, As, panel_b=None, variant="mcqr2gs"):
+        self.As = [colmajor(A) for A in As]
+        self.panel_b = panel_b
+        self.variant = variant
+        dev = self.As[0].device
+        L = load()
+        B = len(self.As)
+        bs = self._panels()
+        ms = (ctypes.c_int64 * B)(*[A.shape[0] for A in self.As])
+        ns = (ctypes.c_int64 * B)(*[A.shape[1] for A in self.As])
+        self.workspace = torch.empty(batched_workspace_size(list(ms), list(ns), list(bs), variant),
+                                     dtype=torch.uint8, device=dev)
+        self.status = torch.zeros(B, dtype=torch.int32, device=dev)
+        self.out = factor_batched(self.As, list(bs), variant, workspace=self.workspace, status=self.status)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._launch()
+
+    def _panels(self):
+        B = len(self.As)
+        pb = self.panel_b if self.panel_b is not None else [0] * B
+        if isinstance(pb, int):
+            pb = [pb] * B
+        return (ctypes.c_int * B)(*[int(b) for b in pb])
+
+    def _launch(self):
+        L = load()
+        B = len(self.As)
+        ms = (ctypes.c_int64 * B)(*[A.shape[0] for A in self.As])
+        ns = (ctypes.c_int64 * B)(*[A.shape[1] for A in self.As])
+        lds = (ctypes.c_int64 * B)(*[_ld(A) for A in self.As])
+        Ap = (ctypes.c_void_p * B)(*[A.data_ptr() for A in self.As])
+        Qp = (ctypes.c_void_p * B)(*[Q.data_ptr() for Q, _ in self.out])
+        Rp = (ctypes.c_void_p * B)(*[R.data_ptr() for _, R in self.out])
+        rc = L.cqr_factor_batched(B, ms, ns, lds, self._panels(), Ap, Qp, Rp, _variant(self.variant),
+                                  _ptr(self.status), _ptr(self.workspace), ctypes.c_size_t(self.workspace.numel()),
+                                  _stream(None))
+        if rc != 0:
+            raise CQRError(rc, "cqr_factor_batched")
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
 
 
 def probe_fp64_peak(iters: int = 4000) -> float:

@@ -337,16 +337,65 @@ int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const doubl
   return 0;
 }
 
-size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant) {
-  if (batch < 0 || (variant != CQR_MCQR2GS && variant != CQR_CQR2GS)) return 0;
-  if (batch > 0 && (!m || !n || !panel_b)) return 0;
+// ---------------------------------------------------------------------------
+// Batched factorisation.  The matrices are spread over a pool of library-owned
+// non-blocking streams (largest work first, each to the least-loaded stream);
+// every stream owns one slice of the workspace.  The pool is forked from the
+// caller's stream with an event and joined back into it, so the whole call is
+// ordered on the caller's stream and can be captured into a CUDA graph.  Each
+// matrix runs exactly the kernel sequence of a single cqr_factor() call with
+// the same sizes and panel width, so its result is bitwise identical; the
+// gain comes from running the small grids, the one-block Cholesky islands and
+// the reductions of different matrices concurrently.
+namespace {
+
+constexpr int kBatchStreams = 16;
+
+struct StreamPool {
+  cudaStream_t s[kBatchStreams];
+  cudaEvent_t done[kBatchStreams];
+  cudaEvent_t fork;
+  int device = -1;
+  bool ok = false;
+};
+StreamPool g_pool[64];  // per device
+
+StreamPool* get_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  StreamPool& p = g_pool[dev];
+  if (!p.ok) {
+    for (int i = 0; i < kBatchStreams; ++i) {
+      if (cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      if (cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    p.device = dev;
+    p.ok = true;
+  }
+  return &p;
+}
+
+size_t batched_slice(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant) {
   size_t mx = 256;
   for (int i = 0; i < batch; ++i) {
     const size_t s = cqr_workspace_size(m[i], n[i], panel_b[i], variant);
     if (s == 0) return 0;
     if (s > mx) mx = s;
   }
-  return mx;
+  return align256(mx);
+}
+
+}  // namespace
+
+size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant) {
+  if (batch < 0 || (variant != CQR_MCQR2GS && variant != CQR_CQR2GS)) return 0;
+  if (batch == 0) return 256;
+  if (!m || !n || !panel_b) return 0;
+  const size_t slice = batched_slice(batch, m, n, panel_b, variant);
+  if (slice == 0) return 0;
+  const int ns = batch < kBatchStreams ? batch : kBatchStreams;
+  return slice * (size_t)ns;
 }
 
 int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* lda, const int* panel_b,
@@ -367,21 +416,60 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
     if (!A[i] || !Q[i] || !R[i]) return -6;
     if (Q[i] != A[i] && overlaps(A[i], lda[i], m[i], n[i], Q[i], lda[i])) return -7;
   }
+  StreamPool* pool = get_pool();
+  if (!pool) return CQR_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   cudaGetLastError();
-  if (cudaMemsetAsync(status, 0, sizeof(int) * batch, st) != cudaSuccess) return CQR_ERR_CUDA;
+  const size_t slice = batched_slice(batch, m, n, panel_b, variant);
+  const int ns = batch < kBatchStreams ? batch : kBatchStreams;
+  // largest work first, each to the least-loaded stream
+  int* order = new int[batch];
+  double* work = new double[batch];
   for (int i = 0; i < batch; ++i) {
+    order[i] = i;
+    work[i] = 4.0 * (double)m[i] * (double)n[i] * (double)n[i];
+  }
+  for (int i = 1; i < batch; ++i) {  // insertion sort by decreasing work (stable)
+    int v = order[i], j = i - 1;
+    while (j >= 0 && work[order[j]] < work[v]) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = v;
+  }
+  double load[kBatchStreams] = {0};
+  int rc = 0;
+  if (cudaMemsetAsync(status, 0, sizeof(int) * batch, st) != cudaSuccess || cudaEventRecord(pool->fork, st) != cudaSuccess)
+    rc = CQR_ERR_CUDA;
+  for (int k = 0; k < ns && rc == 0; ++k)
+    if (cudaStreamWaitEvent(pool->s[k], pool->fork, 0) != cudaSuccess) rc = CQR_ERR_CUDA;
+  for (int q = 0; q < batch && rc == 0; ++q) {
+    const int i = order[q];
+    int k = 0;
+    for (int t = 1; t < ns; ++t)
+      if (load[t] < load[k]) k = t;
+    load[k] += work[i];
+    cudaStream_t s = pool->s[k];
     const int b = resolve_panel(n[i], panel_b[i], variant);
     const Layout L = make_layout(m[i], n[i], b, variant);
-    Work w = bind(workspace, L);
+    Work w = bind((char*)workspace + slice * k, L);
     w.status = status + i;
     if (Q[i] != A[i] && cudaMemcpy2DAsync(Q[i], sizeof(double) * lda[i], A[i], sizeof(double) * lda[i],
-                                          sizeof(double) * m[i], n[i], cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-      return CQR_ERR_CUDA;
-    if (cudaMemsetAsync(R[i], 0, sizeof(double) * n[i] * n[i], st) != cudaSuccess) return CQR_ERR_CUDA;
-    if (factor_run(m[i], n[i], b, Q[i], lda[i], R[i], n[i], variant, w, st) != cudaSuccess) return CQR_ERR_CUDA;
+                                          sizeof(double) * m[i], n[i], cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      rc = CQR_ERR_CUDA;
+    else if (cudaMemsetAsync(R[i], 0, sizeof(double) * n[i] * n[i], s) != cudaSuccess)
+      rc = CQR_ERR_CUDA;
+    else if (factor_run(m[i], n[i], b, Q[i], lda[i], R[i], n[i], variant, w, s) != cudaSuccess)
+      rc = CQR_ERR_CUDA;
   }
-  return 0;
+  // join: the caller's stream waits for every pool stream (also after an error)
+  for (int k = 0; k < ns; ++k) {
+    if (cudaEventRecord(pool->done[k], pool->s[k]) != cudaSuccess || cudaStreamWaitEvent(st, pool->done[k], 0) != cudaSuccess)
+      rc = CQR_ERR_CUDA;
+  }
+  delete[] order;
+  delete[] work;
+  return rc;
 }
 
 const char* cqr_status_string(int status) {

@@ -16,8 +16,10 @@
 // One thread owns one row; 128 rows per block.  The rows live in shared
 // memory, column-major in the row index (conflict-free), and U's upper
 // triangle is packed row by row in shared memory (every thread reads the
-// same U entry: a broadcast).  Columns are solved in groups of eight so
-// that each warp keeps eight independent FMA chains in flight.
+// same U entry: a broadcast).  Columns are solved in groups of sixteen so
+// that each warp keeps sixteen independent FMA chains in flight: with one
+// block of four warps per SM (b = 128 needs 194 KB of shared memory) fewer
+// chains leave the FP64 pipe waiting on dependent FMAs.
 #include "cqr_common.cuh"
 
 namespace cqr {
@@ -25,7 +27,7 @@ namespace cqr {
 namespace {
 
 constexpr int kRows = 128;
-constexpr int kGrp = 8;
+constexpr int kGrp = 16;
 
 __device__ __forceinline__ int packed_off(int i, int b) { return i * b - (i * (i - 1)) / 2; }
 
