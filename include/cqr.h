@@ -48,6 +48,7 @@ enum cqr_variant {
 
 #define CQR_ERR_CUDA (-1000)
 #define CQR_STATUS_TIMEOUT (-2000)
+#define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
 
 /* Largest panel width the library accepts (the one-CTA Cholesky keeps a
  * b x b Gram matrix in shared memory up to 128 and in L2 above). */
@@ -91,6 +92,35 @@ int cqr_default_panel(int64_t n);
  */
 int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
                int64_t ldr, int variant, void* workspace, size_t ws_bytes, cqr_stream_t stream);
+
+/*
+ * cqr_factor_noalloc: cqr_factor() for callers that cannot allocate device
+ * memory when they factor -- code working inside a memory budget fixed at
+ * start-up, code called back from within another framework's allocator or
+ * memory pool, code with a no-allocation-after-initialisation rule.  The
+ * paper has no counterpart; this is a library convenience.
+ *   Arguments 1-10 as in cqr_factor.  There is no workspace argument: the
+ *   scratch is a file-scope device array of CQR_NOALLOC_SCRATCH_BYTES (64 MiB)
+ *   that every GPU which loads the library holds until the process exits.
+ *   status   DEVICE int*: receives the status word (0, breakdown column + 1)
+ *            when the stream reaches the end of the call; NULL = not reported
+ *            (arg 11)
+ *   stream   CUDA stream (arg 12)
+ * Returns the same argument codes as cqr_factor, or
+ * CQR_ERR_NOALLOC_TOO_LARGE when the sizes need more scratch than the array
+ * holds (compare cqr_workspace_size() with CQR_NOALLOC_SCRATCH_BYTES); nothing
+ * is launched then.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents (each call clears what must start at zero), so
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race and give wrong results; order them on one stream
+ * or synchronise between them.  The results are the same as cqr_factor()'s.
+ */
+#define CQR_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int cqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
+                       int64_t ldr, int variant, int* status, cqr_stream_t stream);
 
 /*
  * cqr_read_status: synchronises `stream`, then copies the status word of the

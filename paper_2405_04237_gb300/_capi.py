@@ -19,12 +19,14 @@ MCQR2GS, CQR2GS, CQR2, SCQR3 = 0, 1, 2, 3
 VARIANTS = {"mcqr2gs": MCQR2GS, "cqr2gs": CQR2GS, "cqr2": CQR2, "scqr3": SCQR3}
 ERR_CUDA = -1000
 STATUS_TIMEOUT = -2000
+ERR_NOALLOC_TOO_LARGE = -3000
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTS = [
     "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status",
     "cqr_backward_workspace_size", "cqr_backward", "cqr_batched_workspace_size",
     "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak",
-    "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
+    "cqr_factor_noalloc", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
 ]
 KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "adjoint_misc",
                   "batched"]
@@ -63,6 +65,7 @@ def load(build_if_missing: bool = True):
             "cqr_default_panel": (c_int, [i64]),
             "cqr_factor": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, sz, vp]),
             "cqr_read_status": (c_int, [vp, vp, PI]),
+            "cqr_factor_noalloc": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, vp]),
             "cqr_backward_workspace_size": (sz, [i64, i64]),
             "cqr_backward": (c_int, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64, vp, sz, vp]),
             "cqr_batched_workspace_size": (sz, [c_int, P64, P64, PI, c_int]),

@@ -4,6 +4,8 @@
 // caller's stream; nothing here computes on the host, allocates, or waits.
 #include <string.h>
 
+#include <mutex>
+
 #include "cqr.h"
 #include "cqr_common.cuh"
 
@@ -472,8 +474,76 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
   return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free factorisation.  Some callers cannot allocate device memory
+// at the point where they factor: code running under a fixed memory budget
+// planned once at start-up, code called back from inside another
+// framework's allocator or memory pool, or code with a rule that nothing
+// allocates after initialisation.  For them the scratch that cqr_factor()
+// takes as a caller-supplied workspace lives in this file-scope device array
+// instead: it is created when the library is loaded and held by every GPU
+// that loads the library until the process exits.
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[CQR_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};  // device address of g_noalloc_scratch, per device
+
+// First call on a device: look up the array's device address with that
+// device current (in host code the array's name is not a device address).
+void* noalloc_scratch() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return nullptr;
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+}  // namespace
+
+int cqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
+                       int64_t ldr, int variant, int* status, cqr_stream_t stream) {
+  if (m < 1 || m < n) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (variant < 0 || variant > 3) return -10;
+  const int b = resolve_panel(n, panel_b, variant);
+  if (panel_b < 0 || b < 1 || b > CQR_MAX_PANEL || n % b) return -5;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return -2;
+  if (!Q) return -6;
+  if (ldq < m || (Q == A && ldq != lda)) return -7;
+  if (Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
+  if (!R) return -8;
+  if (ldr < n) return -9;
+  const Layout L = make_layout(m, n, b, variant);
+  if (L.total > (size_t)CQR_NOALLOC_SCRATCH_BYTES) return CQR_ERR_NOALLOC_TOO_LARGE;
+  void* scratch = noalloc_scratch();
+  if (!scratch) return CQR_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Work w = bind(scratch, L);
+  cudaGetLastError();
+  // The array keeps the previous call's contents: the status word must start at 0.
+  if (cudaMemsetAsync(w.status, 0, sizeof(int), st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (Q != A && cudaMemcpy2DAsync(Q, sizeof(double) * ldq, A, sizeof(double) * lda, sizeof(double) * m, n,
+                                  cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (status && cudaMemcpyAsync(status, w.status, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  return 0;
+}
+
 const char* cqr_status_string(int status) {
   if (status == 0) return "success";
+  if (status == CQR_ERR_NOALLOC_TOO_LARGE)
+    return "cqr_factor_noalloc: the factorisation needs more scratch than the fixed CQR_NOALLOC_SCRATCH_BYTES array";
   if (status == CQR_ERR_CUDA) return "a CUDA launch or copy failed";
   if (status == CQR_STATUS_TIMEOUT) return "a bounded wait in the batched persistent kernel expired";
   if (status > 0) return "Cholesky breakdown: the Gram matrix is not numerically positive definite (status = column + 1)";
