@@ -46,6 +46,16 @@ enum cqr_variant {
   CQR_SCQR3 = 3    /* Alg. 5: shifted CholeskyQR (Alg. 4) then CholeskyQR2, R = R2 R1 (b = n) */
 };
 
+/* Flag OR-ed into `variant` of cqr_factor (MCQR2GS, CQR2GS): look-ahead, the
+ * overlap of each trailing update with the next panel's CholeskyQR that
+ * Sec. 7 names as future work.  The update of step j is split: the next
+ * panel's columns on `stream`, the rest concurrently on a library-owned side
+ * stream joined back with an event before the next projection.  Results are
+ * bitwise identical to the default schedule.  Off by default: on GB300 the
+ * path is bound by the FP64 pipe with almost no idle gaps, so the overlap
+ * measured no gain (20,000 x 64 to 2^21 x 1024). */
+#define CQR_LOOKAHEAD 0x100
+
 #define CQR_ERR_CUDA (-1000)
 #define CQR_STATUS_TIMEOUT (-2000)
 #define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
@@ -80,7 +90,7 @@ int cqr_default_panel(int64_t n);
  *              must not overlap A                                   (args 6, 7)
  *   R, ldr     output n x n upper triangular with positive diagonal;
  *              its strict lower triangle is zeroed; ldr >= n        (args 8, 9)
- *   variant    enum cqr_variant                                     (arg 10)
+ *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD         (arg 10)
  *   workspace  device buffer of ws_bytes >= cqr_workspace_size()    (args 11, 12)
  *   stream     CUDA stream                                          (arg 13)
  * Panel loop (Alg. 9): for each panel j the Gram W_j = A_j^T A_j (Alg. 1

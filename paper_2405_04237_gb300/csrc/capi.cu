@@ -84,7 +84,7 @@ Work bind(void* ws, const Layout& L) {
     if (e_ != cudaSuccess) return e_;     \
   } while (0)
 
-// X := X U^{-1} for any width: 128-column blocks, the coupling between
+// X := X U^{-1} for any width: kTrsmMaxB-column blocks, the coupling between
 // blocks applied as an FMA update in ascending column order (so each element
 // sees the same operation sequence as plain substitution).
 cudaError_t trsm_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
@@ -123,26 +123,68 @@ cudaError_t cqr_panel(i64 m, int b, double* X, i64 ldx, double* U, i64 ldu, cons
   return cudaSuccess;
 }
 
+// Look-ahead (the overlap of the trailing update with the next panel's
+// CholeskyQR that Sec. 7 lists as future work).  When a side stream is
+// given, the update of step j is split: the next panel's b columns are
+// updated first on the caller's stream, so its CQR (and, in Alg. 9, its
+// re-orthogonalisation) starts at once, while the rest of the trailing
+// update runs concurrently on the side stream; the next projection waits
+// for it.  Each element still receives the same FMA sequence, so the
+// results are bitwise those of the unsplit schedule; the overlap fills the
+// GPU during the serial Cholesky islands, reductions and launch gaps.
+struct Side {
+  cudaStream_t s;
+  cudaEvent_t to_side, to_main;
+};
+
+// A_{j:k} -= Qp Y with the split above.  Y is b x wd with leading dim ldy.
+cudaError_t split_update(i64 m, int b, i64 wd, const double* Qp, i64 ldq, const double* Y, i64 ldy, double* Aj,
+                         i64 lda, const int* status, cudaStream_t st, const Side* side, bool* pending) {
+  if (side && wd > b) {
+    TRY(cudaEventRecord(side->to_side, st));
+    TRY(cudaStreamWaitEvent(side->s, side->to_side, 0));
+    TRY(nn_product(m, (int)(wd - b), b, Qp, ldq, Y + (i64)b * ldy, ldy, Aj + (i64)b * lda, lda, -1.0, 1, 0, 0,
+                   status, side->s));
+    TRY(cudaEventRecord(side->to_main, side->s));
+    *pending = true;
+    return nn_product(m, b, b, Qp, ldq, Y, ldy, Aj, lda, -1.0, 1, 0, 0, status, st);
+  }
+  return nn_product(m, (int)wd, b, Qp, ldq, Y, ldy, Aj, lda, -1.0, 1, 0, 0, status, st);
+}
+
+cudaError_t join_side(cudaStream_t st, const Side* side, bool* pending) {
+  if (side && *pending) {
+    *pending = false;
+    return cudaStreamWaitEvent(st, side->to_main, 0);
+  }
+  return cudaSuccess;
+}
+
 // Alg. 6 on X (m x n, in place), panels of width b; R (ldr) pre-zeroed.
-cudaError_t cqrgs_run(i64 m, i64 n, int b, double* X, i64 ldx, double* R, i64 ldr, const Work& w, cudaStream_t st) {
+cudaError_t cqrgs_run(i64 m, i64 n, int b, double* X, i64 ldx, double* R, i64 ldr, const Work& w, cudaStream_t st,
+                      const Side* side) {
   const i64 k = n / b;
+  bool pending = false;
   for (i64 j = 0; j < k; ++j) {
     const i64 jb = j * b;
     double* Xj = X + jb * ldx;
     TRY(cqr_panel(m, b, Xj, ldx, R + jb + jb * ldr, ldr, w, (int)jb, 0, st));
     const i64 wd = n - jb - b;
     if (wd > 0) {
+      TRY(join_side(st, side, &pending));  // the rest of the previous update
       double* Yp = R + jb + (jb + b) * ldr;  // Y lands in R_{j,j+1:k}
       TRY(tn_product(m, b, (int)wd, Xj, ldx, Xj + (i64)b * ldx, ldx, 0, w.part, Yp, ldr, w.status, st));
-      TRY(nn_product(m, (int)wd, b, Xj, ldx, Yp, ldr, Xj + (i64)b * ldx, ldx, -1.0, 1, 0, 0, w.status, st));
+      TRY(split_update(m, b, wd, Xj, ldx, Yp, ldr, Xj + (i64)b * ldx, ldx, w.status, st, side, &pending));
     }
   }
-  return cudaSuccess;
+  return join_side(st, side, &pending);
 }
 
 // Alg. 9 on Q (m x n, in place); R (ldr) pre-zeroed.
-cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w, cudaStream_t st) {
+cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w, cudaStream_t st,
+                        const Side* side) {
   const i64 k = n / b;
+  bool pending = false;
   // step 1: [Q_1, R_11] = CQR2(A_1)
   TRY(cqr_panel(m, b, Q, ldq, w.S1, b, w, 0, 0, st));
   TRY(cqr_panel(m, b, Q, ldq, w.S2, b, w, 0, 0, st));
@@ -153,8 +195,9 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
     double* Aj = Q + jb * ldq;
     double* Yp = R + (jb - b) + jb * ldr;
     // steps 3-5: Y = Q_{j-1}^T A_{j:k}; A_{j:k} -= Q_{j-1} Y; R_{j-1,j:k} = Y
+    TRY(join_side(st, side, &pending));
     TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
-    TRY(nn_product(m, (int)wd, b, Qprev, ldq, Yp, ldr, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    TRY(split_update(m, b, wd, Qprev, ldq, Yp, ldr, Aj, ldq, w.status, st, side, &pending));
     // step 6: [P, S1] = CQR(A_j)
     TRY(cqr_panel(m, b, Aj, ldq, w.S1, b, w, (int)jb, 0, st));
     // step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z
@@ -166,19 +209,19 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
     TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R + jb + jb * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
     TRY(nn_product(jb, b, b, w.Z, jb, w.S1, b, R + jb * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
   }
-  return cudaSuccess;
+  return join_side(st, side, &pending);
 }
 
 cudaError_t factor_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, int variant, const Work& w,
-                       cudaStream_t st) {
+                       cudaStream_t st, const Side* side = nullptr) {
   switch (variant) {
     case CQR_MCQR2GS:
-      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st);
+      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st, side);
     case CQR_CQR2GS:
       TRY(cudaMemsetAsync(w.R1, 0, sizeof(double) * n * n, st));
       TRY(cudaMemsetAsync(w.R2, 0, sizeof(double) * n * n, st));
-      TRY(cqrgs_run(m, n, b, Q, ldq, w.R1, n, w, st));
-      TRY(cqrgs_run(m, n, b, Q, ldq, w.R2, n, w, st));
+      TRY(cqrgs_run(m, n, b, Q, ldq, w.R1, n, w, st, side));
+      TRY(cqrgs_run(m, n, b, Q, ldq, w.R2, n, w, st, side));
       return nn_product(n, (int)n, (int)n, w.R2, n, w.R1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
     case CQR_CQR2:
       TRY(cqr_panel(m, (int)n, Q, ldq, w.S1, n, w, 0, 0, st));
@@ -193,6 +236,26 @@ cudaError_t factor_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 l
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+// Per-device side stream for the look-ahead of single factorisations.  The
+// enqueue of one factorisation holds the mutex, so concurrent host threads
+// do not interleave their event records.
+std::mutex g_side_mu;
+Side g_side[64];
+bool g_side_ok[64] = {};
+
+const Side* get_side() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!g_side_ok[dev]) {
+    Side& s = g_side[dev];
+    if (cudaStreamCreateWithFlags(&s.s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&s.to_side, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&s.to_main, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    g_side_ok[dev] = true;
+  }
+  return &g_side[dev];
 }
 
 bool overlaps(const double* a, i64 lda, i64 m, i64 n, const double* b, i64 ldb) {
@@ -231,7 +294,9 @@ size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant) {
 }
 
 int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
-               int64_t ldr, int variant, void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+               int64_t ldr, int variant_flags, void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+  const bool lookahead = (variant_flags & CQR_LOOKAHEAD) != 0;
+  const int variant = variant_flags & ~CQR_LOOKAHEAD;
   if (m < 1 || m < n) return -1;
   if (n < 1) return -2;
   if (!A) return -3;
@@ -256,7 +321,14 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
                                   cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return CQR_ERR_CUDA;
   if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
-  if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (lookahead && (variant == CQR_MCQR2GS || variant == CQR_CQR2GS)) {
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    const Side* side = get_side();
+    if (!side) return CQR_ERR_CUDA;
+    if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st, side) != cudaSuccess) return CQR_ERR_CUDA;
+  } else if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st) != cudaSuccess) {
+    return CQR_ERR_CUDA;
+  }
   return 0;
 }
 
