@@ -56,6 +56,17 @@ enum cqr_variant {
  * measured no gain (20,000 x 64 to 2^21 x 1024). */
 #define CQR_LOOKAHEAD 0x100
 
+/* Flag OR-ed into `variant` of cqr_factor (MCQR2GS only; other variants give
+ * argument error -10): the runtime choice of how many CholeskyQR passes a
+ * panel gets, the optimisation Sec. 7 proposes.  For the second pass of each
+ * panel (Alg. 3 step 2 on panel 1, Alg. 9 step 8 on the others), if every
+ * entry of its Cholesky factor S2 lies within 8u of the identity (u = 2^-53),
+ * the panel is already orthonormal to working precision: S2 := I exactly
+ * and the triangular solve is skipped (decided on the device, no host
+ * synchronisation).  Only nearly orthonormal panels qualify: on the paper's
+ * test matrices the rule fires for kappa ~ 1 and never for kappa >= 1e2. */
+#define CQR_ADAPTIVE 0x200
+
 #define CQR_ERR_CUDA (-1000)
 #define CQR_STATUS_TIMEOUT (-2000)
 #define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
@@ -90,7 +101,7 @@ int cqr_default_panel(int64_t n);
  *              must not overlap A                                   (args 6, 7)
  *   R, ldr     output n x n upper triangular with positive diagonal;
  *              its strict lower triangle is zeroed; ldr >= n        (args 8, 9)
- *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD         (arg 10)
+ *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD, | CQR_ADAPTIVE (arg 10)
  *   workspace  device buffer of ws_bytes >= cqr_workspace_size()    (args 11, 12)
  *   stream     CUDA stream                                          (arg 13)
  * Panel loop (Alg. 9): for each panel j the Gram W_j = A_j^T A_j (Alg. 1

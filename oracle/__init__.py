@@ -37,6 +37,7 @@ _lock = threading.Lock()
 _lib = None
 
 LITERAL_R = 1  # or_mcqr2gs flag: drop the R_{1:j-1,j} += Z S1 term
+ADAPTIVE = 2   # or_mcqr2gs flag: runtime choice of the second CholeskyQR pass (Sec. 7)
 
 
 def build(force: bool = False) -> str:
@@ -226,13 +227,15 @@ def cqr2gs(A, b, check=True):
     return _ret(Q, R, st, check, "cqr2gs")
 
 
-def mcqr2gs(A, b, check=True, literal_r=False):
-    """Alg. 9 (modified CholeskyQR2 with Gram-Schmidt), panel width b."""
+def mcqr2gs(A, b, check=True, literal_r=False, adaptive=False):
+    """Alg. 9 (modified CholeskyQR2 with Gram-Schmidt), panel width b.
+    adaptive=True: the runtime choice of the second CholeskyQR pass (Sec. 7)."""
     lib = _load()
     A = _f64(A)
     m, n = A.shape
     R = np.zeros((n, n), order="F")
-    st = lib.or_mcqr2gs(m, n, int(b), _p(A), max(m, 1), _p(R), n, LITERAL_R if literal_r else 0)
+    flags = (LITERAL_R if literal_r else 0) | (ADAPTIVE if adaptive else 0)
+    st = lib.or_mcqr2gs(m, n, int(b), _p(A), max(m, 1), _p(R), n, flags)
     return _ret(A, R, int(st), check, "mcqr2gs")
 
 

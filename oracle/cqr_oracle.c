@@ -311,6 +311,35 @@ int or_cqr2gs(i64 m, i64 n, i64 b, double* X, i64 ldx, double* R, i64 ldr) {
 }
 
 #define OR_FLAG_LITERAL_R 1 /* R_jj = S2 S1 only; drop the R_{1:j-1,j} += Z S1 term */
+#define OR_FLAG_ADAPTIVE 2  /* runtime choice of the second CholeskyQR pass (Sec. 7), see below */
+
+/* Runtime choice of CholeskyQR repetitions (the future work of Sec. 7).
+ * The second pass of a panel (Alg. 3 step 2 for the first panel, Alg. 9
+ * step 8 for the others) forms W = P^T P and its Cholesky factor S2.  When
+ * every entry of S2 - I is within 8u, P is already orthonormal to working
+ * precision: S2 is replaced by I exactly and the triangular solve, which
+ * would then leave P unchanged, is not performed.  Returns 1 when skipped. */
+static int adaptive_second_pass(i64 m, i64 b, double* X, i64 ldx, double* S, i64 lds, int* st) {
+  double* W = (double*)malloc(sizeof(double) * (size_t)(b * b));
+  or_gram(m, b, X, ldx, W, b);
+  *st = or_chol(b, W, b, S, lds);
+  free(W);
+  if (*st) return 0;
+  const double tau = 8.0 * ldexp(1.0, -53);
+  int near_identity = 1;
+  for (i64 c = 0; c < b && near_identity; ++c)
+    for (i64 r = 0; r <= c; ++r) {
+      double d = AT(S, lds, r, c) - (r == c ? 1.0 : 0.0);
+      if (!(fabs(d) <= tau)) { near_identity = 0; break; }
+    }
+  if (near_identity) {
+    for (i64 c = 0; c < b; ++c)
+      for (i64 r = 0; r < b; ++r) AT(S, lds, r, c) = (r == c) ? 1.0 : 0.0;
+    return 1;
+  }
+  or_trsm(m, b, X, ldx, S, lds);
+  return 0;
+}
 
 /* Alg. 9 (modified CholeskyQR2 with Gram-Schmidt), panels of width b, k = n/b:
  *   [Q_1, R_11] = CQR2(A_1)
@@ -332,7 +361,17 @@ int or_mcqr2gs(i64 m, i64 n, i64 b, double* X, i64 ldx, double* R, i64 ldr, int 
   double* S2 = (double*)malloc(sizeof(double) * (size_t)(b * b));
   double* Z = (double*)malloc(sizeof(double) * (size_t)(n * b));
   double* ZS = (double*)malloc(sizeof(double) * (size_t)(n * b));
-  int st = or_cqr2(m, b, X, ldx, R, ldr);
+  int st;
+  if (flags & OR_FLAG_ADAPTIVE) {
+    /* first panel: CQR, then the adaptive second pass; R_11 = S2 S1 */
+    st = or_cqr(m, b, X, ldx, S1, b);
+    if (!st) {
+      adaptive_second_pass(m, b, X, ldx, S2, b, &st);
+      if (!st) small_mm(b, b, b, S2, b, 1, S1, b, 1, R, ldr);
+    }
+  } else {
+    st = or_cqr2(m, b, X, ldx, R, ldr);
+  }
   for (i64 j = 1; j < k && !st; ++j) {
     double* Qprev = X + (j - 1) * b * ldx;
     double* Aj = X + j * b * ldx;
@@ -345,7 +384,10 @@ int or_mcqr2gs(i64 m, i64 n, i64 b, double* X, i64 ldx, double* R, i64 ldr, int 
     i64 jb = j * b;
     or_tn(m, jb, b, X, ldx, Aj, ldx, Z, jb);
     or_update(m, jb, b, Aj, ldx, X, ldx, Z, jb);
-    st = or_cqr(m, b, Aj, ldx, S2, b);
+    if (flags & OR_FLAG_ADAPTIVE)
+      adaptive_second_pass(m, b, Aj, ldx, S2, b, &st);
+    else
+      st = or_cqr(m, b, Aj, ldx, S2, b);
     if (st) { st += (int)(j * b); break; }
     small_mm(b, b, b, S2, b, 1, S1, b, 1, &AT(R, ldr, jb, jb), ldr);
     if (!(flags & OR_FLAG_LITERAL_R)) {

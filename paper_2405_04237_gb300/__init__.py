@@ -93,12 +93,14 @@ def read_status(workspace: torch.Tensor, stream=None) -> int:
 
 
 def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: bool = False, check: bool = True,
-           out=None, workspace: torch.Tensor | None = None, stream=None, lookahead: bool = False):
+           out=None, workspace: torch.Tensor | None = None, stream=None, lookahead: bool = False,
+           adaptive: bool = False):
     """A = Q R.  Returns (Q, R) as column-major FP64 tensors.
 
     inplace=True overwrites A's (column-major) storage with Q.  lookahead=True
     overlaps each trailing update with the next panel's CholeskyQR on a side
-    stream (bitwise-identical results).  check=True
+    stream (bitwise-identical results).  adaptive=True (mCQR2GS) applies the
+    runtime choice of the second CholeskyQR pass per panel.  check=True
     synchronises the stream and raises CQRError on a Cholesky breakdown; with
     check=False the call is fully asynchronous (and graph-capturable when a
     workspace and outputs are supplied).
@@ -124,7 +126,7 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
         raise ValueError(f"workspace too small: {workspace.numel()} < {ws_bytes}")
     st = _stream(stream)
     rc = L.cqr_factor(m, n, _ptr(Ac), _ld(Ac), int(panel_b), _ptr(Q), _ld(Q), _ptr(R), _ld(R),
-                      var | (_capi.LOOKAHEAD if lookahead else 0),
+                      var | (_capi.LOOKAHEAD if lookahead else 0) | (_capi.ADAPTIVE if adaptive else 0),
                       _ptr(workspace), ctypes.c_size_t(workspace.numel()), st)
     if rc != 0:
         raise CQRError(rc, "cqr_factor")

@@ -16,7 +16,7 @@ namespace {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t status, W, S1, S2, rinv, Z, R1, R2, part, total;
+  size_t status, skip, W, S1, S2, rinv, Z, R1, R2, part, total;
 };
 
 // Workspace plan.  The status word sits at offset 0 (cqr_read_status).
@@ -31,6 +31,7 @@ Layout make_layout(i64 m, i64 n, int b, int variant) {
   const bool whole = (variant == CQR_CQR2 || variant == CQR_SCQR3);
   const i64 pw = whole ? n : b;  // panel width of every CQR
   L.status = take(sizeof(int));
+  L.skip = take(sizeof(int));
   L.W = take(sizeof(double) * pw * pw);
   L.S1 = take(sizeof(double) * pw * pw);
   L.S2 = take(sizeof(double) * pw * pw);
@@ -60,6 +61,7 @@ Layout make_layout(i64 m, i64 n, int b, int variant) {
 
 struct Work {
   int* status;
+  int* skip;  // second-pass decision of the runtime repetition choice
   double *W, *S1, *S2, *rinv, *Z, *R1, *R2, *part;
 };
 
@@ -67,6 +69,7 @@ Work bind(void* ws, const Layout& L) {
   char* p = (char*)ws;
   Work w;
   w.status = (int*)(p + L.status);
+  w.skip = (int*)(p + L.skip);
   w.W = (double*)(p + L.W);
   w.S1 = (double*)(p + L.S1);
   w.S2 = (double*)(p + L.S2);
@@ -88,12 +91,12 @@ Work bind(void* ws, const Layout& L) {
 // blocks applied as an FMA update in ascending column order (so each element
 // sees the same operation sequence as plain substitution).
 cudaError_t trsm_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
-                     const int* status, cudaStream_t st) {
+                     const int* status, cudaStream_t st, const int* skip = nullptr) {
   for (int c0 = 0; c0 < b; c0 += kTrsmMaxB) {
     const int cb = b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB;
     if (c0 > 0)
       TRY(nn_product(m, cb, c0, X, ldx, U + (i64)c0 * ldu, ldu, X + (i64)c0 * ldx, ldx, -1.0, 1, 0, 0, status, st));
-    TRY(trsm_rows(m, cb, X + (i64)c0 * ldx, ldx, U + c0 + (i64)c0 * ldu, ldu, rinv + c0, status, st));
+    TRY(trsm_rows(m, cb, X + (i64)c0 * ldx, ldx, U + c0 + (i64)c0 * ldu, ldu, rinv + c0, status, st, skip));
   }
   return cudaSuccess;
 }
@@ -115,11 +118,14 @@ cudaError_t trsm_t_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ld
 }
 
 // Alg. 1 on the m x b panel X (in place): W = X^T X; W = U^T U; X := X U^{-1}.
+// `second_pass_rule`: the runtime repetition choice (Sec. 7) for a second
+// CholeskyQR pass -- U within 8u of I becomes I and the solve is skipped.
 cudaError_t cqr_panel(i64 m, int b, double* X, i64 ldx, double* U, i64 ldu, const Work& w, int col0, int shift,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool second_pass_rule = false) {
+  int* skip = second_pass_rule ? w.skip : nullptr;
   TRY(tn_product(m, b, b, X, ldx, X, ldx, 1, w.part, w.W, b, w.status, st));
-  TRY(chol_factor(b, w.W, b, U, ldu, w.rinv, col0, w.status, shift, m, st));
-  TRY(trsm_any(m, b, X, ldx, U, ldu, w.rinv, w.status, st));
+  TRY(chol_factor(b, w.W, b, U, ldu, w.rinv, col0, w.status, shift, m, st, skip));
+  TRY(trsm_any(m, b, X, ldx, U, ldu, w.rinv, w.status, st, skip));
   return cudaSuccess;
 }
 
@@ -182,12 +188,12 @@ cudaError_t cqrgs_run(i64 m, i64 n, int b, double* X, i64 ldx, double* R, i64 ld
 
 // Alg. 9 on Q (m x n, in place); R (ldr) pre-zeroed.
 cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w, cudaStream_t st,
-                        const Side* side) {
+                        const Side* side, bool adaptive) {
   const i64 k = n / b;
   bool pending = false;
   // step 1: [Q_1, R_11] = CQR2(A_1)
   TRY(cqr_panel(m, b, Q, ldq, w.S1, b, w, 0, 0, st));
-  TRY(cqr_panel(m, b, Q, ldq, w.S2, b, w, 0, 0, st));
+  TRY(cqr_panel(m, b, Q, ldq, w.S2, b, w, 0, 0, st, adaptive));
   TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R, ldr, 1.0, 0, 1, 1, w.status, st));
   for (i64 j = 1; j < k; ++j) {
     const i64 jb = j * b, wd = n - jb;
@@ -204,7 +210,7 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
     TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
     TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
     // step 8: [Q_j, S2] = CQR(P)
-    TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st));
+    TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st, adaptive));
     // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
     TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R + jb + jb * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
     TRY(nn_product(jb, b, b, w.Z, jb, w.S1, b, R + jb * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
@@ -213,10 +219,10 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
 }
 
 cudaError_t factor_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, int variant, const Work& w,
-                       cudaStream_t st, const Side* side = nullptr) {
+                       cudaStream_t st, const Side* side = nullptr, bool adaptive = false) {
   switch (variant) {
     case CQR_MCQR2GS:
-      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st, side);
+      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st, side, adaptive);
     case CQR_CQR2GS:
       TRY(cudaMemsetAsync(w.R1, 0, sizeof(double) * n * n, st));
       TRY(cudaMemsetAsync(w.R2, 0, sizeof(double) * n * n, st));
@@ -296,7 +302,8 @@ size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant) {
 int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
                int64_t ldr, int variant_flags, void* workspace, size_t ws_bytes, cqr_stream_t stream) {
   const bool lookahead = (variant_flags & CQR_LOOKAHEAD) != 0;
-  const int variant = variant_flags & ~CQR_LOOKAHEAD;
+  const bool adaptive = (variant_flags & CQR_ADAPTIVE) != 0;
+  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE);
   if (m < 1 || m < n) return -1;
   if (n < 1) return -2;
   if (!A) return -3;
@@ -321,12 +328,13 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
                                   cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return CQR_ERR_CUDA;
   if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (adaptive && variant != CQR_MCQR2GS) return -10;
   if (lookahead && (variant == CQR_MCQR2GS || variant == CQR_CQR2GS)) {
     std::lock_guard<std::mutex> lk(g_side_mu);
     const Side* side = get_side();
     if (!side) return CQR_ERR_CUDA;
-    if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st, side) != cudaSuccess) return CQR_ERR_CUDA;
-  } else if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st) != cudaSuccess) {
+    if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st, side, adaptive) != cudaSuccess) return CQR_ERR_CUDA;
+  } else if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st, nullptr, adaptive) != cudaSuccess) {
     return CQR_ERR_CUDA;
   }
   return 0;

@@ -64,8 +64,11 @@ cudaError_t nn_product_t(i64 M, int N, int K, const double* A, i64 lda, const do
 // On breakdown at local column j, status is set to col0 + j + 1 (first
 // breakdown wins) and U_jj onward are NaN.  `shift_fro` != 0 applies the
 // shifted-CholeskyQR shift s = sqrt(m) * 2^-53 * trace(W) first (Alg. 4).
+// With `skip` non-null the second-pass rule of the runtime repetition
+// choice applies: if every entry of U - I is within 8u, U := I exactly and
+// *skip = 1 (else 0).
 cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* rinv, int col0, int* status,
-                        int shift_fro, i64 m, cudaStream_t st);
+                        int shift_fro, i64 m, cudaStream_t st, int* skip = nullptr);
 
 // ---------------------------------------------------------------------------
 // Row-wise forward substitution  X := X U^{-1}  (X m x b, b <= kTrsmMaxB),
@@ -75,8 +78,9 @@ cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* r
 // and U would fill the shared memory with one block of four warps
 // (b = 128: 0.78 -> 1.13 TFLOP/s on GB300).
 constexpr int kTrsmMaxB = 64;
+// With `skip` non-null and *skip set on the device, the launch does nothing.
 cudaError_t trsm_rows(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
-                      const int* status, cudaStream_t st);
+                      const int* status, cudaStream_t st, const int* skip = nullptr);
 
 // Row-wise back substitution  X := X U^{-T}  (X m x b, b <= kTrsmMaxB): solves
 // Abar U^T = B for the adjoint.  rinv as above.

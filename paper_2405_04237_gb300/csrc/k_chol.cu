@@ -28,7 +28,8 @@ constexpr int kCholThreads = 512;
 
 template <bool SMEM>
 __global__ void __launch_bounds__(kCholThreads) chol_kernel(int b, double* W, i64 ldw, double* U, i64 ldu,
-                                                            double* rinv, int col0, int* status, int shift, i64 m) {
+                                                            double* rinv, int col0, int* status, int shift, i64 m,
+                                                            int* skip) {
   extern __shared__ __align__(16) double sm[];
   if (status && *status) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = kCholThreads / 32;
@@ -36,9 +37,13 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(int b, double* W, i6
   double* rv = sm + b;          // [b]  reciprocals
   double* Ws = sm + 2 * b;      // [b*b] row-major (SMEM only)
   __shared__ int broken;
+  __shared__ int far_from_identity;
   // element (a, c), a <= c
   auto at = [&](int a, int c) -> double& { return SMEM ? Ws[a * b + c] : W[a + (i64)c * ldw]; };
-  if (t == 0) broken = -1;
+  if (t == 0) {
+    broken = -1;
+    far_from_identity = 0;
+  }
   if (SMEM) {
     for (int e = t; e < b * b; e += kCholThreads) {
       const int a = e % b, c = e / b;
@@ -92,14 +97,34 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(int b, double* W, i6
     __syncthreads();
   }
   const int jb = broken;
+  // Runtime choice of the second CholeskyQR pass (Sec. 7): when every entry
+  // of U - I is within 8u the panel is already orthonormal to working
+  // precision; U becomes I exactly and the triangular solve is skipped
+  // (with U = I it would leave the panel unchanged).
+  bool identity = false;
+  if (skip) {
+    if (jb < 0) {
+      const double tau = 8.0 * 0x1p-53;
+      for (int e = t; e < b * b; e += kCholThreads) {
+        const int a = e % b, c = e / b;
+        if (a <= c && !(fabs(at(a, c) - (a == c ? 1.0 : 0.0)) <= tau)) far_from_identity = 1;
+      }
+    }
+    __syncthreads();
+    identity = (jb < 0) && !far_from_identity;
+    if (t == 0) *skip = identity ? 1 : 0;
+  }
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   for (int e = t; e < b * b; e += kCholThreads) {
     const int a = e % b, c = e / b;
     double v = 0.0;
-    if (a <= c) v = (jb >= 0 && a >= jb) ? nan : at(a, c);
+    if (identity)
+      v = (a == c) ? 1.0 : 0.0;
+    else if (a <= c)
+      v = (jb >= 0 && a >= jb) ? nan : at(a, c);
     U[a + (i64)c * ldu] = v;
   }
-  for (int e = t; e < b; e += kCholThreads) rinv[e] = (jb >= 0 && e >= jb) ? nan : rv[e];
+  for (int e = t; e < b; e += kCholThreads) rinv[e] = identity ? 1.0 : ((jb >= 0 && e >= jb) ? nan : rv[e]);
 }
 
 // M := copyltu(T - G): M_ac = T_ac - G_ac for a >= c, mirrored above.
@@ -134,7 +159,7 @@ __global__ void probe_kernel(int iters, double a, double b) {
 }  // namespace
 
 cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* rinv, int col0, int* status,
-                        int shift_fro, i64 m, cudaStream_t st) {
+                        int shift_fro, i64 m, cudaStream_t st, int* skip) {
   if (b <= 0) return cudaSuccess;
   if (b <= 128) {
     const size_t smem = sizeof(double) * ((size_t)2 * b + (size_t)b * b);
@@ -145,12 +170,12 @@ cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* r
       attr = true;
     }
     prof_begin(kCholesky, st);
-    chol_kernel<true><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m);
+    chol_kernel<true><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m, skip);
     prof_end(kCholesky, (double)b * b * b / 3.0, st);
   } else {
     const size_t smem = sizeof(double) * (size_t)2 * b;
     prof_begin(kCholesky, st);
-    chol_kernel<false><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m);
+    chol_kernel<false><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m, skip);
     prof_end(kCholesky, (double)b * b * b / 3.0, st);
   }
   return cudaGetLastError();

@@ -48,9 +48,10 @@ __device__ __forceinline__ void load_common(int b, const double* U, i64 ldu, con
 }
 
 __global__ void __launch_bounds__(kRows) trsm_rows_kernel(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu,
-                                                          const double* rinv, const int* status) {
+                                                          const double* rinv, const int* status, const int* skip) {
   extern __shared__ __align__(16) double sm[];
   if (status && *status) return;
+  if (skip && *skip) return;  // U = I: the solve would leave X unchanged
   double* Ts = sm;
   double* Up = sm + (size_t)b * kRows;
   double* rv = Up + b * (b + 1) / 2 + kGrp;
@@ -150,13 +151,13 @@ void set_trsm_attr() {
 }  // namespace
 
 cudaError_t trsm_rows(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
-                      const int* status, cudaStream_t st) {
+                      const int* status, cudaStream_t st, const int* skip) {
   if (m <= 0 || b <= 0) return cudaSuccess;
   if (b > kTrsmMaxB) return cudaErrorInvalidValue;
   set_trsm_attr();
   const i64 blocks = (m + kRows - 1) / kRows;
   prof_begin(kTrsm, st);
-  trsm_rows_kernel<<<(unsigned)blocks, kRows, trsm_smem(b), st>>>(m, b, X, ldx, U, ldu, rinv, status);
+  trsm_rows_kernel<<<(unsigned)blocks, kRows, trsm_smem(b), st>>>(m, b, X, ldx, U, ldu, rinv, status, skip);
   prof_end(kTrsm, (double)m * b * b, st);
   return cudaGetLastError();
 }

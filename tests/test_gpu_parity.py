@@ -148,6 +148,25 @@ def test_lookahead_is_bitwise_identical(cuda_lib, variant, b):
     assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2)
 
 
+@pytest.mark.parametrize("kappa", [1.0, 1e10])
+def test_adaptive_repetitions_match_oracle(cuda_lib, oracle, kappa):
+    """Runtime choice of the second CholeskyQR pass (Sec. 7): at kappa = 1 the
+    rule fires on every panel (both sides), at 1e10 never; parity with the
+    oracle's adaptive mode either way."""
+    A = make_test_matrix(30000, 64, kappa, seed=1504)
+    Qg, Rg = gpu_factor(cuda_lib, A, 16, "mcqr2gs", adaptive=True)
+    Qo, Ro = oracle.mcqr2gs(A, 16, adaptive=True)
+    assert orth_err(Qg) <= ORTH_TOL and resid(A, Qg, Rg) <= RES_TOL
+    if kappa <= 1e6:
+        assert rel_diff(Rg, Ro) <= R_TOL and np.abs(Qg - Qo).max() <= Q_TOL
+    if kappa == 1.0:  # skipped passes: R_jj = S1 exactly, so S2 = I on both sides
+        Qd, Rd = gpu_factor(cuda_lib, A, 16, "mcqr2gs")
+        assert not np.array_equal(Qd, Qg)
+    else:
+        Qd, Rd = gpu_factor(cuda_lib, A, 16, "mcqr2gs")
+        assert np.array_equal(Qd, Qg) and np.array_equal(Rd, Rg)
+
+
 def test_side_stream(cuda_lib):
     A = make_test_matrix(20000, 32, 1e4, seed=1502)
     Q1, R1 = gpu_factor(cuda_lib, A, 8, "mcqr2gs")

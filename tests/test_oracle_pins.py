@@ -259,6 +259,30 @@ def test_literal_r_reading_is_rounding_level(oracle):
     assert 2 * resid(A, Q, R) < resid(A, Ql, Rl) < 1e-13
 
 
+# --------------------------------------------------------------------------- runtime CQR repetition choice
+@pytest.mark.parametrize("kappa", [1e4, 1e15])
+def test_adaptive_rule_silent_on_ill_conditioned_panels(oracle, kappa):
+    """Sec. 7 (runtime choice of the number of CholeskyQR repetitions): the
+    second pass is skipped only when its factor is within 8u of I.  Panels of
+    the paper's test matrices with kappa >= 1e2 never qualify, so the result
+    is bitwise the default one."""
+    A = make_test_matrix(20000, 64, kappa, seed=51)
+    Q, R = oracle.mcqr2gs(A, 16)
+    Qa, Ra = oracle.mcqr2gs(A, 16, adaptive=True)
+    assert np.array_equal(Q, Qa) and np.array_equal(R, Ra)
+
+
+def test_adaptive_rule_fires_on_orthonormal_panels(oracle):
+    """kappa = 1: after the first pass every panel is orthonormal to working
+    precision, the second pass is skipped, and the result stays O(u)."""
+    A = make_test_matrix(20000, 64, 1.0, seed=52)
+    Q, R = oracle.mcqr2gs(A, 16)
+    Qa, Ra = oracle.mcqr2gs(A, 16, adaptive=True)
+    assert not np.array_equal(Q, Qa)  # the rule did change the computation
+    assert orth_err(Qa) < 1e-14 and resid(A, Qa, Ra) < 1e-15
+    assert np.abs(Qa - Q).max() < 1e-15 and rel_diff(Ra, R) < 1e-15
+
+
 # --------------------------------------------------------------------------- adjoint
 def _loss_grad_fd(oracle, A, dQ, dR, b, h):
     G = np.zeros_like(A)
