@@ -67,6 +67,19 @@ enum cqr_variant {
  * test matrices the rule fires for kappa ~ 1 and never for kappa >= 1e2. */
 #define CQR_ADAPTIVE 0x200
 
+/* Flag OR-ed into `variant` of cqr_factor and cqr_workspace_size (MCQR2GS
+ * only): the m-row projections Y = Q_{j-1}^T A_{j:k} and Z = Q_{1:j-1}^T P
+ * (Alg. 9 steps 3 and 7) run on the FP8 tensor cores with an error-free
+ * splitting of the FP64 operands (Ozaki scheme): per 4096-row sub-chunk each
+ * column is scaled by a power of two and cut into 14 signed 4-bit digits
+ * (56 bits), the 105 most significant digit-plane pairs are multiplied
+ * exactly (FP32 accumulation of integers < 2^24) and recombined in FP64.
+ * Not FP64 arithmetic, but FP64-accurate: the truncation drops terms below
+ * about 2^-52 of the column scales.  All other steps stay native FP64.  The
+ * workspace grows (cqr_workspace_size with the flag) by the digit planes of
+ * one row chunk (about 1 GiB) and one FP64 partial per 4096 rows. */
+#define CQR_EMULATED 0x400
+
 #define CQR_ERR_CUDA (-1000)
 #define CQR_STATUS_TIMEOUT (-2000)
 #define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
@@ -78,7 +91,8 @@ enum cqr_variant {
 /*
  * cqr_workspace_size: bytes of device workspace cqr_factor() needs for an
  * m x n factorisation with panel width panel_b (0 = library default, see
- * cqr_default_panel) and the given variant.  Returns 0 for invalid sizes.
+ * cqr_default_panel) and the given variant (with its CQR_EMULATED flag, if
+ * any).  Returns 0 for invalid sizes.
  */
 size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant);
 
@@ -101,7 +115,8 @@ int cqr_default_panel(int64_t n);
  *              must not overlap A                                   (args 6, 7)
  *   R, ldr     output n x n upper triangular with positive diagonal;
  *              its strict lower triangle is zeroed; ldr >= n        (args 8, 9)
- *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD, | CQR_ADAPTIVE (arg 10)
+ *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD, CQR_ADAPTIVE,
+ *              CQR_EMULATED                                          (arg 10)
  *   workspace  device buffer of ws_bytes >= cqr_workspace_size()    (args 11, 12)
  *   stream     CUDA stream                                          (arg 13)
  * Panel loop (Alg. 9): for each panel j the Gram W_j = A_j^T A_j (Alg. 1

@@ -74,8 +74,9 @@ def default_panel(n: int) -> int:
     return int(load().cqr_default_panel(int(n)))
 
 
-def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs") -> int:
-    return int(load().cqr_workspace_size(int(m), int(n), int(panel_b), _variant(variant)))
+def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs", emulated: bool = False) -> int:
+    return int(load().cqr_workspace_size(int(m), int(n), int(panel_b),
+                                         _variant(variant) | (_capi.EMULATED if emulated else 0)))
 
 
 def batched_workspace_size(ms, ns, panel_b, variant="mcqr2gs") -> int:
@@ -94,13 +95,15 @@ def read_status(workspace: torch.Tensor, stream=None) -> int:
 
 def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: bool = False, check: bool = True,
            out=None, workspace: torch.Tensor | None = None, stream=None, lookahead: bool = False,
-           adaptive: bool = False):
+           adaptive: bool = False, emulated: bool = False):
     """A = Q R.  Returns (Q, R) as column-major FP64 tensors.
 
     inplace=True overwrites A's (column-major) storage with Q.  lookahead=True
     overlaps each trailing update with the next panel's CholeskyQR on a side
     stream (bitwise-identical results).  adaptive=True (mCQR2GS) applies the
-    runtime choice of the second CholeskyQR pass per panel.  check=True
+    runtime choice of the second CholeskyQR pass per panel.  emulated=True
+    (mCQR2GS) runs the m-row projections on the FP8 tensor cores with the
+    FP64-accurate Ozaki splitting.  check=True
     synchronises the stream and raises CQRError on a Cholesky breakdown; with
     check=False the call is fully asynchronous (and graph-capturable when a
     workspace and outputs are supplied).
@@ -117,7 +120,9 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
     else:
         Q = Ac if inplace else empty_colmajor(m, n, A.device)
         R = empty_colmajor(n, n, A.device)
-    ws_bytes = L.cqr_workspace_size(m, n, int(panel_b), var)
+    flags = var | (_capi.LOOKAHEAD if lookahead else 0) | (_capi.ADAPTIVE if adaptive else 0) | (
+        _capi.EMULATED if emulated else 0)
+    ws_bytes = L.cqr_workspace_size(m, n, int(panel_b), flags)
     if ws_bytes == 0:
         raise CQRError(-5 if n > 0 and m >= n else -1, "cqr_workspace_size")
     if workspace is None:
@@ -125,8 +130,7 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
     elif workspace.numel() < ws_bytes:
         raise ValueError(f"workspace too small: {workspace.numel()} < {ws_bytes}")
     st = _stream(stream)
-    rc = L.cqr_factor(m, n, _ptr(Ac), _ld(Ac), int(panel_b), _ptr(Q), _ld(Q), _ptr(R), _ld(R),
-                      var | (_capi.LOOKAHEAD if lookahead else 0) | (_capi.ADAPTIVE if adaptive else 0),
+    rc = L.cqr_factor(m, n, _ptr(Ac), _ld(Ac), int(panel_b), _ptr(Q), _ld(Q), _ptr(R), _ld(R), flags,
                       _ptr(workspace), ctypes.c_size_t(workspace.numel()), st)
     if rc != 0:
         raise CQRError(rc, "cqr_factor")

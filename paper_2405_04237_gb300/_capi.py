@@ -18,6 +18,7 @@ _lib = None
 MCQR2GS, CQR2GS, CQR2, SCQR3 = 0, 1, 2, 3
 LOOKAHEAD = 0x100
 ADAPTIVE = 0x200
+EMULATED = 0x400
 VARIANTS = {"mcqr2gs": MCQR2GS, "cqr2gs": CQR2GS, "cqr2": CQR2, "scqr3": SCQR3}
 ERR_CUDA = -1000
 STATUS_TIMEOUT = -2000

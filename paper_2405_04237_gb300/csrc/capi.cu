@@ -16,11 +16,11 @@ namespace {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t status, skip, W, S1, S2, rinv, Z, R1, R2, part, total;
+  size_t status, skip, W, S1, S2, rinv, Z, R1, R2, part, oz, total;
 };
 
 // Workspace plan.  The status word sits at offset 0 (cqr_read_status).
-Layout make_layout(i64 m, i64 n, int b, int variant) {
+Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -55,6 +55,16 @@ Layout make_layout(i64 m, i64 n, int b, int variant) {
     }
   }
   L.part = take(sizeof(double) * pd);
+  size_t oz = 0;
+  if (emulated && variant == CQR_MCQR2GS) {  // projections Y (b x w) and Z (jb x b) of Alg. 9
+    for (i64 j = 1; j * b < n; ++j) {
+      size_t d = ozaki_workspace_bytes(m, b, (int)(n - j * b));
+      if (d > oz) oz = d;
+      d = ozaki_workspace_bytes(m, (int)(j * b), b);
+      if (d > oz) oz = d;
+    }
+  }
+  L.oz = take(oz);
   L.total = off;
   return L;
 }
@@ -63,6 +73,7 @@ struct Work {
   int* status;
   int* skip;  // second-pass decision of the runtime repetition choice
   double *W, *S1, *S2, *rinv, *Z, *R1, *R2, *part;
+  void* oz;   // emulated projections (null: native FP64)
 };
 
 Work bind(void* ws, const Layout& L) {
@@ -78,6 +89,7 @@ Work bind(void* ws, const Layout& L) {
   w.R1 = (double*)(p + L.R1);
   w.R2 = (double*)(p + L.R2);
   w.part = (double*)(p + L.part);
+  w.oz = nullptr;
   return w;
 }
 
@@ -202,12 +214,18 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
     double* Yp = R + (jb - b) + jb * ldr;
     // steps 3-5: Y = Q_{j-1}^T A_{j:k}; A_{j:k} -= Q_{j-1} Y; R_{j-1,j:k} = Y
     TRY(join_side(st, side, &pending));
-    TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
+    if (w.oz)
+      TRY(tn_product_emulated(m, b, (int)wd, Qprev, ldq, Aj, ldq, w.oz, Yp, ldr, w.status, st));
+    else
+      TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
     TRY(split_update(m, b, wd, Qprev, ldq, Yp, ldr, Aj, ldq, w.status, st, side, &pending));
     // step 6: [P, S1] = CQR(A_j)
     TRY(cqr_panel(m, b, Aj, ldq, w.S1, b, w, (int)jb, 0, st));
     // step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z
-    TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
+    if (w.oz)
+      TRY(tn_product_emulated(m, (int)jb, b, Q, ldq, Aj, ldq, w.oz, w.Z, jb, w.status, st));
+    else
+      TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
     TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
     // step 8: [Q_j, S2] = CQR(P)
     TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st, adaptive));
@@ -291,19 +309,23 @@ static int resolve_panel(int64_t n, int panel_b, int variant) {
   return panel_b == 0 ? cqr_default_panel(n) : panel_b;
 }
 
-size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant) {
+size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant_flags) {
+  const bool emulated = (variant_flags & CQR_EMULATED) != 0;
+  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED);
   if (m < 1 || n < 1 || m < n || variant < 0 || variant > 3) return 0;
   const int b = resolve_panel(n, panel_b, variant);
   if (b < 1 || b > CQR_MAX_PANEL || n % b) return 0;
   if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return 0;
-  return make_layout(m, n, b, variant).total;
+  if (emulated && variant != CQR_MCQR2GS) return 0;
+  return make_layout(m, n, b, variant, emulated).total;
 }
 
 int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
                int64_t ldr, int variant_flags, void* workspace, size_t ws_bytes, cqr_stream_t stream) {
   const bool lookahead = (variant_flags & CQR_LOOKAHEAD) != 0;
   const bool adaptive = (variant_flags & CQR_ADAPTIVE) != 0;
-  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE);
+  const bool emulated = (variant_flags & CQR_EMULATED) != 0;
+  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED);
   if (m < 1 || m < n) return -1;
   if (n < 1) return -2;
   if (!A) return -3;
@@ -318,10 +340,12 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   if (!R) return -8;
   if (ldr < n) return -9;
   if (!workspace || ((uintptr_t)workspace & 255)) return -11;
-  const Layout L = make_layout(m, n, b, variant);
+  if (emulated && variant != CQR_MCQR2GS) return -10;
+  const Layout L = make_layout(m, n, b, variant, emulated);
   if (ws_bytes < L.total) return -12;
   cudaStream_t st = (cudaStream_t)stream;
-  const Work w = bind(workspace, L);
+  Work w = bind(workspace, L);
+  if (emulated) w.oz = (char*)workspace + L.oz;
   cudaGetLastError();  // clear stale errors from earlier, unrelated calls
   if (cudaMemsetAsync(w.status, 0, sizeof(int), st) != cudaSuccess) return CQR_ERR_CUDA;
   if (Q != A && cudaMemcpy2DAsync(Q, sizeof(double) * ldq, A, sizeof(double) * lda, sizeof(double) * m, n,

@@ -45,6 +45,13 @@ size_t tn_partial_doubles(i64 m, int p, int q, int sym);  // S * p * q
 cudaError_t tn_product(i64 m, int p, int q, const double* X, i64 ldx, const double* Y, i64 ldy, int sym,
                        double* part, double* C, i64 ldc, const int* status, cudaStream_t st);
 
+// FP64-accurate C = X^T Y on the FP8 tensor cores (k_ozaki.cu): the m-row
+// sum of the projections with the Ozaki splitting.  `ws` must hold
+// ozaki_workspace_bytes(m, p, q) bytes.
+size_t ozaki_workspace_bytes(i64 m, int p, int q);
+cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, const double* Y, i64 ldy,
+                                void* ws, double* C, i64 ldc, const int* status, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // C (M x N) = beta*C + alpha * A (M x K) * B (K x N), alpha = +-1, beta in
 // {0, 1}.  When beta == 1 the sum starts from C and each term is applied
