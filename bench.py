@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint sub-benchmarks")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-check", action="store_true", help="skip the accuracy norms")
+    p.add_argument("--emulated", action="store_true",
+                   help="time the emulated variant (projections on FP8 tensor cores) instead of native FP64")
     return p.parse_args()
 
 
@@ -359,10 +361,11 @@ def run_ours(args, dist, rank, world):
     A = make_test_matrix_cuda(m, n, kappa, SEED_FULL + 100 * rank)
     Q = P.empty_colmajor(m, n, "cuda")
     R = P.empty_colmajor(n, n, "cuda")
-    ws = torch.empty(P.workspace_size(m, n, b, "mcqr2gs"), dtype=torch.uint8, device="cuda")
+    emu = bool(args.emulated)
+    ws = torch.empty(P.workspace_size(m, n, b, "mcqr2gs", emulated=emu), dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     for i in range(args.warmup):
-        P.factor(A, b, out=(Q, R), workspace=ws, check=(i == 0))
+        P.factor(A, b, out=(Q, R), workspace=ws, check=(i == 0), emulated=emu)
     torch.cuda.synchronize()
     probe = P.probe_fp64_peak(20000)  # clocks are warm now
     stream = torch.cuda.current_stream()
@@ -373,7 +376,7 @@ def run_ours(args, dist, rank, world):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            P.factor(A, b, out=(Q, R), workspace=ws, check=False, stream=stream)
+            P.factor(A, b, out=(Q, R), workspace=ws, check=False, stream=stream, emulated=emu)
         e1.record(stream)
         e1.synchronize()
     torch.cuda.synchronize()
@@ -422,7 +425,7 @@ def run_ours(args, dist, rank, world):
         e0.record(stream)
         for _ in range(args.steps):
             Ad.copy_(Ah, non_blocking=True)
-            P.factor(Ad, b, out=(Q, R), workspace=ws, check=False, stream=stream)
+            P.factor(Ad, b, out=(Q, R), workspace=ws, check=False, stream=stream, emulated=emu)
             Qh.copy_(Q, non_blocking=True)
             Rh.copy_(R, non_blocking=True)
         e1.record(stream)
@@ -460,7 +463,8 @@ def run_ours(args, dist, rank, world):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"mCQR2GS m={m} n={n} kappa={kappa:.0e} b={b} (out of place)", "m": m, "n": n,
+            "config": {"workload": f"mCQR2GS m={m} n={n} kappa={kappa:.0e} b={b} (out of place)"
+                                   + (", projections emulated on FP8 tensor cores" if emu else ""), "m": m, "n": n,
                        "kappa": kappa, "panel_b": b, "variant": "mcqr2gs",
                        "l2": f"inputs larger than L2 ({8 * m * n / 1e9:.1f} GB), no flush",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},

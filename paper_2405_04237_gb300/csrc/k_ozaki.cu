@@ -9,7 +9,9 @@
 // integer |x| * 2^(56 - e_c) (truncated below 2^-56 of the scale) split into
 // 14 unsigned nibbles n_0..n_13 (n_i has weight 16^i); digit i of x is
 // sign(x) * n_i, an integer in [-15, 15] that e4m3 represents exactly.
-// Digits of one sub-chunk live in 14 "planes", K-contiguous per column.
+// Digits live in 14 "planes" laid out [sub-chunk][32-row stage][plane]
+// [column][32 bytes], so that one stage of a 32-column tile is 14
+// contiguous 1 KiB runs per operand.
 //
 // Products.  x_a y_b = 2^(e_a + e_b - 112) sum_{i,j} d^x_i d^y_j 16^(i+j).
 // The 105 plane pairs with i + j >= 13 (the 14 most significant weight
@@ -20,8 +22,10 @@
 //
 // Schedule.  A block (7 warps) computes a 32 x 32 tile of C for one
 // sub-chunk: warp w owns levels 13 + w and 26 - w (15 plane pairs, equal for
-// every warp), the planes of 64 rows are staged in shared memory, and at the
-// end each warp converts its two exact level sums to FP64 with the scales,
+// every warp); the planes of 32 rows are staged in shared memory by
+// asynchronous copies, two stages deep, so the next stage streams in while
+// the tensor cores work on the current one; at the end each warp converts its
+// two exact level sums to FP64 with the scales,
 // the seven warps' values are added in a fixed order, and the tile is written
 // as the sub-chunk's partial.  A fixed-order sum over sub-chunks gives C.
 #include "cqr_common.cuh"
@@ -35,8 +39,10 @@ constexpr int kPlanes = 14;         // nibbles: 56 bits
 constexpr int kOzWarps = 7;
 constexpr int kOzThreads = 32 * kOzWarps;
 constexpr int kTile = 32;           // output tile (p and q)
-constexpr int kStage = 64;          // rows per shared-memory stage
+constexpr int kStage = 32;          // rows per shared-memory stage (one k32 MMA step)
 constexpr int kLdk = kStage + 16;   // bytes per column row in shared memory (conflict-free fragments)
+constexpr int kBufBytes = 2 * kPlanes * kTile * kLdk;  // one stage of both operands
+constexpr int kStagesPerSub = kSub / kStage;
 constexpr int kExpZero = -100000;   // scale of an all-zero column
 constexpr int kExpBad = 100000;     // a column holding Inf or NaN
 
@@ -51,7 +57,8 @@ __device__ __forceinline__ uint32_t e4m3_of_nibble(uint32_t n) {
 // Splitting: X (rows r0 .. r0 + nsub*kSub of an m x c matrix) -> planes.
 // Grid (nsub, c); 256 threads; thread t handles rows 16t .. 16t+15 of the
 // sub-chunk as four words of four consecutive rows.
-// planes layout: [(s * kPlanes + i) * c + col][kSub] bytes; exps: [s * c + col].
+// planes layout: byte ((s * kStagesPerSub + st) * kPlanes + i) * c * 32 +
+// col * 32 + (row in stage); exps: [s * c + col].
 __global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c,
                                                           uint8_t* planes, int* exps, const int* status) {
   if (status && *status) return;
@@ -112,13 +119,21 @@ __global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 l
       }
     }
   }
-  const i64 pstride = (i64)c * kSub;
+  const int st = (16 * t) / kStage, inrow = (16 * t) % kStage;
+  uint8_t* dst = planes + ((i64)s * kStagesPerSub + st) * kPlanes * c * kStage + (i64)col * kStage + inrow;
 #pragma unroll
   for (int i = 0; i < kPlanes; ++i) {
     uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
-    *reinterpret_cast<uint4*>(planes + (i64)s * kPlanes * pstride + i * pstride + (i64)col * kSub + 16 * t) = v;
+    *reinterpret_cast<uint4*>(dst + (i64)i * c * kStage) = v;
   }
 }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_e4m3(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
@@ -149,11 +164,6 @@ __global__ void __launch_bounds__(kOzThreads, 2) ozaki_tn_kernel(OzArgs a) {
   const int p0 = blockIdx.y * kTile, q0 = blockIdx.z * kTile;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int g = lane >> 2, tq = lane & 3;
-  uint8_t* sx = osm;                                 // [kPlanes][kTile][kLdk]
-  uint8_t* sy = osm + kPlanes * kTile * kLdk;        // [kPlanes][kTile][kLdk]
-  const i64 pstride_x = (i64)a.p * kSub, pstride_y = (i64)a.q * kSub;
-  const uint8_t* bx = a.px + (i64)s * kPlanes * pstride_x;
-  const uint8_t* by = a.py + (i64)s * kPlanes * pstride_y;
   const int lvA = 13 + warp, lvB = 26 - warp;        // weight levels i + j of this warp
   float accA[2][4][4], accB[2][4][4];
 #pragma unroll
@@ -163,36 +173,56 @@ __global__ void __launch_bounds__(kOzThreads, 2) ozaki_tn_kernel(OzArgs a) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) accA[mi][ni][r] = accB[mi][ni][r] = 0.f;
 
-  for (int k0 = 0; k0 < kSub; k0 += kStage) {
-    // stage planes: 2 operands x 14 planes x 32 columns x 64 bytes, 16-byte pieces
-    for (int e = t; e < 2 * kPlanes * kTile * (kStage / 16); e += kOzThreads) {
-      const int piece = e % (kStage / 16);
-      const int colp = (e / (kStage / 16)) % kTile;
-      const int pl = (e / (kStage / 16 * kTile)) % kPlanes;
-      const int op = e / (kStage / 16 * kTile * kPlanes);
-      const int colg = (op == 0 ? p0 : q0) + colp;
-      const int lim = op == 0 ? a.p : a.q;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (colg < lim) {
-        const uint8_t* src = (op == 0 ? bx + pl * pstride_x : by + pl * pstride_y) + (i64)colg * kSub + k0 + 16 * piece;
-        v = *reinterpret_cast<const uint4*>(src);
-      }
-      uint8_t* dst = (op == 0 ? sx : sy) + (pl * kTile + colp) * kLdk + 16 * piece;
-      *reinterpret_cast<uint4*>(dst) = v;
-    }
-    __syncthreads();
+  // Per-thread copy plan of one stage (identical for every stage up to the
+  // stage base): 2 operands x 14 planes x 32 columns x 32 bytes = 1792
+  // pieces of 16 bytes, 8 per thread.
+  constexpr int kPieces = 2 * kPlanes * kTile * (kStage / 16);
+  constexpr int kPer = kPieces / kOzThreads;
+  static_assert(kPieces % kOzThreads == 0, "copy plan");
+  int src_off[kPer];  // within one stage of one operand (< 14 * 1024 * 32 bytes); -1: beyond the last column
+  int dst_off[kPer];
 #pragma unroll
-    for (int kk = 0; kk < kStage; kk += 32) {
-      // plane i of X against planes j = lvA - i and lvB - i of Y
-#pragma unroll 1
-      for (int i = 0; i < kPlanes; ++i) {
-        const int jA = lvA - i, jB = lvB - i;
-        const bool useA = jA >= 0 && jA < kPlanes, useB = jB >= 0 && jB < kPlanes;
-        if (!useA && !useB) continue;
+  for (int k = 0; k < kPer; ++k) {
+    const int e = t + k * kOzThreads;
+    const int op = e / (kPieces / 2);
+    const int r = e % (kPieces / 2);
+    const int pl = r / (kTile * 2), within = r % (kTile * 2);
+    const int colp = within >> 1, piece = within & 1;
+    const int c = op == 0 ? a.p : a.q;
+    const int colg = (op == 0 ? p0 : q0) + colp;
+    src_off[k] = colg < c ? pl * c * kStage + colg * kStage + 16 * piece : -1;
+    dst_off[k] = (op * kPlanes * kTile + pl * kTile + colp) * kLdk + 16 * piece;
+  }
+  const i64 stage_x = (i64)kPlanes * a.p * kStage, stage_y = (i64)kPlanes * a.q * kStage;
+  const uint8_t* bx = a.px + (i64)s * kStagesPerSub * stage_x;
+  const uint8_t* by = a.py + (i64)s * kStagesPerSub * stage_y;
+  auto issue = [&](int st, uint8_t* buf) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = t + k * kOzThreads;
+      const uint8_t* src = (e < kPieces / 2 ? bx + st * stage_x : by + st * stage_y) + (src_off[k] < 0 ? 0 : src_off[k]);
+      cp_async16(buf + dst_off[k], src, src_off[k] < 0 ? 0 : 16);  // zero fill beyond the last column
+    }
+  };
+  issue(0, osm);
+  cp_async_commit();
+  for (int st = 0; st < kStagesPerSub; ++st) {
+    if (st + 1 < kStagesPerSub) issue(st + 1, osm + ((st + 1) & 1) * kBufBytes);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const uint8_t* sx = osm + (st & 1) * kBufBytes + (16 * 0 + g) * kLdk + 4 * tq;   // + (i*kTile + 16 mi) * kLdk
+    const uint8_t* sy = osm + (st & 1) * kBufBytes + (kPlanes * kTile + g) * kLdk + 4 * tq;
+    // plane i of X against planes j = lvA - i and lvB - i of Y (warp-uniform predicates)
+#pragma unroll
+    for (int i = 0; i < kPlanes; ++i) {
+      const int jA = lvA - i, jB = lvB - i;
+      const bool useA = jA < kPlanes, useB = jB < kPlanes;  // j >= 0 always holds (lvA, lvB >= 13)
+      if (useA || useB) {
         uint32_t af[2][4];
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi) {
-          const uint8_t* base = sx + (i * kTile + 16 * mi + g) * kLdk + kk + 4 * tq;
+          const uint8_t* base = sx + (i * kTile + 16 * mi) * kLdk;
           af[mi][0] = *reinterpret_cast<const uint32_t*>(base);
           af[mi][1] = *reinterpret_cast<const uint32_t*>(base + 8 * kLdk);
           af[mi][2] = *reinterpret_cast<const uint32_t*>(base + 16);
@@ -201,7 +231,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) ozaki_tn_kernel(OzArgs a) {
         if (useA) {
 #pragma unroll
           for (int ni = 0; ni < 4; ++ni) {
-            const uint8_t* bb = sy + (jA * kTile + 8 * ni + g) * kLdk + kk + 4 * tq;
+            const uint8_t* bb = sy + (jA * kTile + 8 * ni) * kLdk;
             const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bb);
             const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bb + 16);
 #pragma unroll
@@ -211,7 +241,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) ozaki_tn_kernel(OzArgs a) {
         if (useB) {
 #pragma unroll
           for (int ni = 0; ni < 4; ++ni) {
-            const uint8_t* bb = sy + (jB * kTile + 8 * ni + g) * kLdk + kk + 4 * tq;
+            const uint8_t* bb = sy + (jB * kTile + 8 * ni) * kLdk;
             const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bb);
             const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bb + 16);
 #pragma unroll
@@ -220,7 +250,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) ozaki_tn_kernel(OzArgs a) {
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // the buffer is refilled two stages later
   }
   // this warp's two exact level sums -> FP64 (weights 16^lv, exact powers of two)
   double* red = reinterpret_cast<double*>(osm);  // [kOzWarps][kTile * kTile]
@@ -266,7 +296,7 @@ __global__ void ozaki_reduce_kernel(const double* part, i64 nsub, int p, int q, 
 }
 
 inline size_t oz_smem() {
-  const size_t planes = (size_t)2 * kPlanes * kTile * kLdk;
+  const size_t planes = (size_t)2 * kBufBytes;
   const size_t red = sizeof(double) * kOzWarps * kTile * kTile;
   return planes > red ? planes : red;
 }
