@@ -56,12 +56,13 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
   }
   L.part = take(sizeof(double) * pd);
   size_t oz = 0;
-  if (emulated && variant == CQR_MCQR2GS) {  // projections Y (b x w) and Z (jb x b) of Alg. 9
+  if (emulated && variant == CQR_MCQR2GS) {  // products with Y (b x w) and Z (jb x b) of Alg. 9
     for (i64 j = 1; j * b < n; ++j) {
-      size_t d = ozaki_workspace_bytes(m, b, (int)(n - j * b));
-      if (d > oz) oz = d;
-      d = ozaki_workspace_bytes(m, (int)(j * b), b);
-      if (d > oz) oz = d;
+      const size_t d[4] = {ozaki_workspace_bytes(m, b, (int)(n - j * b)), ozaki_workspace_bytes(m, (int)(j * b), b),
+                           ozaki_nn_workspace_bytes(m, (int)(n - j * b), b),
+                           ozaki_nn_workspace_bytes(m, b, (int)(j * b))};
+      for (size_t x : d)
+        if (x > oz) oz = x;
     }
   }
   L.oz = take(oz);
@@ -73,7 +74,7 @@ struct Work {
   int* status;
   int* skip;  // second-pass decision of the runtime repetition choice
   double *W, *S1, *S2, *rinv, *Z, *R1, *R2, *part;
-  void* oz;   // emulated projections (null: native FP64)
+  void* oz;   // emulated projections and updates (null: native FP64)
 };
 
 Work bind(void* ws, const Layout& L) {
@@ -218,7 +219,10 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
       TRY(tn_product_emulated(m, b, (int)wd, Qprev, ldq, Aj, ldq, w.oz, Yp, ldr, w.status, st));
     else
       TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
-    TRY(split_update(m, b, wd, Qprev, ldq, Yp, ldr, Aj, ldq, w.status, st, side, &pending));
+    if (w.oz)  // the emulated update uses w.oz, so it stays on this stream (no look-ahead split)
+      TRY(nn_update_emulated(m, (int)wd, b, Qprev, ldq, Yp, ldr, Aj, ldq, w.oz, w.status, st));
+    else
+      TRY(split_update(m, b, wd, Qprev, ldq, Yp, ldr, Aj, ldq, w.status, st, side, &pending));
     // step 6: [P, S1] = CQR(A_j)
     TRY(cqr_panel(m, b, Aj, ldq, w.S1, b, w, (int)jb, 0, st));
     // step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z
@@ -226,7 +230,10 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
       TRY(tn_product_emulated(m, (int)jb, b, Q, ldq, Aj, ldq, w.oz, w.Z, jb, w.status, st));
     else
       TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
-    TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    if (w.oz)
+      TRY(nn_update_emulated(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, w.oz, w.status, st));
+    else
+      TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
     // step 8: [Q_j, S2] = CQR(P)
     TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st, adaptive));
     // R_jj = S2 S1;  R_{1:j-1,j} += Z S1

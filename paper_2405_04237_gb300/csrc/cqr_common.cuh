@@ -51,6 +51,12 @@ cudaError_t tn_product(i64 m, int p, int q, const double* X, i64 ldx, const doub
 size_t ozaki_workspace_bytes(i64 m, int p, int q);
 cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, const double* Y, i64 ldy,
                                 void* ws, double* C, i64 ldc, const int* status, cudaStream_t st);
+// FP64-accurate C (M x N, ldc) -= X (M x K) Y (K x N) on the FP8 tensor
+// cores: the m-row updates of the emulated variant.  `ws` must hold
+// ozaki_nn_workspace_bytes(M, N, K) bytes.
+size_t ozaki_nn_workspace_bytes(i64 M, int N, int K);
+cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, const double* Y, i64 ldy, double* C,
+                               i64 ldc, void* ws, const int* status, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // C (M x N) = beta*C + alpha * A (M x K) * B (K x N), alpha = +-1, beta in
