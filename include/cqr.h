@@ -23,8 +23,9 @@
  *     status word kept at the start of the workspace; read it with
  *     cqr_read_status() (synchronous) after the stream work completes.
  *     Status codes: 0 = ok; j+1 (> 0) = breakdown at global column j of the
- *     factorisation; CQR_STATUS_TIMEOUT = a bounded wait of the batched
- *     persistent kernel expired.  After a breakdown, every later kernel of
+ *     factorisation; CQR_STATUS_TIMEOUT = a bounded wait inside a kernel
+ *     (an mbarrier of the emulated products) expired.  After a breakdown,
+ *     every later kernel of
  *     the same call returns immediately and Q, R are undefined.
  */
 #ifndef CQR_GB300_H

@@ -656,7 +656,7 @@ const char* cqr_status_string(int status) {
   if (status == CQR_ERR_NOALLOC_TOO_LARGE)
     return "cqr_factor_noalloc: the factorisation needs more scratch than the fixed CQR_NOALLOC_SCRATCH_BYTES array";
   if (status == CQR_ERR_CUDA) return "a CUDA launch or copy failed";
-  if (status == CQR_STATUS_TIMEOUT) return "a bounded wait in the batched persistent kernel expired";
+  if (status == CQR_STATUS_TIMEOUT) return "a bounded wait inside a kernel expired";
   if (status > 0) return "Cholesky breakdown: the Gram matrix is not numerically positive definite (status = column + 1)";
   return "invalid argument (status = -(argument position))";
 }

@@ -1,43 +1,57 @@
-// FP64-accurate split-m products on the FP8 tensor cores (the Ozaki
-// error-free splitting; Ozaki, Ogita, Oishi, Numer. Algorithms 59 (2012)),
-// for the emulated variant of Alg. 9 (opt-in, CQR_EMULATED): the projections
-// C = X^T Y of steps 3 and 7 and the updates C -= X Y of steps 4 and 7.
+// FP64-accurate split-m products on the 5th-generation (tcgen05) FP8 tensor
+// cores, with the Ozaki error-free splitting (Ozaki, Ogita, Oishi, Numer.
+// Algorithms 59 (2012)), for the emulated variant of Alg. 9 (opt-in,
+// CQR_EMULATED): the projections C = X^T Y of steps 3 and 7 and the updates
+// C -= X Y of steps 4 and 7.
 //
 // Splitting.  For C = X^T Y, rows are cut into sub-chunks of kSub = 4096.
 // Within a sub-chunk every column c of X (and of Y) gets a power-of-two
-// scale 2^e_c with |x| < 2^e_c, and each entry becomes the 56-bit
-// fixed-point integer |x| * 2^(56 - e_c) (truncated below 2^-56 of the scale)
-// split into 14 unsigned nibbles n_0..n_13 (n_i has weight 16^i); digit i of
-// x is sign(x) * n_i, an integer in [-15, 15] that e4m3 represents exactly.
-// Digits live in 14 "planes" laid out [sub-chunk][32-row stage][plane]
-// [column][32 bytes], so that one stage of a 32-column tile is 14
-// contiguous 1 KiB runs per operand.  For C -= X Y the contraction runs over
-// the columns of X: each row of X gets its own scale over (at most kSub of)
-// its entries and its digits take the place of a column in the same layout;
-// Y (K x N) is split by columns as before.
+// scale 2^e_c with |x| < 2^e_c, and each entry becomes the 56-bit fixed-point
+// integer |x| * 2^(56 - e_c) (truncated below 2^-56 of the scale) split into
+// 14 unsigned nibbles n_0..n_13 (n_i has weight 16^i); digit i of x is
+// sign(x) * n_i, an integer in [-15, 15] that e4m3 represents exactly.  For
+// C -= X Y the contraction runs over the columns of X: each row of X gets its
+// own scale over (at most kSub of) its entries and takes a column's place;
+// Y (K x N) is split by columns.
+//
+// Plane layout.  One "stage" is 32 contraction indices.  For stage st and
+// plane i the digits of all columns form one block of cp * 32 bytes (cp =
+// the column count rounded up to the tile), in the tensor cores' canonical
+// K-major layout without swizzling: 8-column groups of 256 bytes, each two
+// 8 x 16-byte core matrices (indices 0..15, then 16..31).  A 128-column tile
+// of one plane is thus one contiguous 4 KiB run and a 32-column tile one
+// 1 KiB run, which the kernel fetches with plain bulk asynchronous copies.
 //
 // Products.  x_a y_b = 2^(e_a + e_b - 112) sum_{i,j} d^x_i d^y_j 16^(i+j).
-// The plane pairs with i + j >= kLevelLo (the 27 - kLevelLo most significant
-// weight levels) are multiplied with mma.sync m16n8k32 e4m3 -> f32.  Per
-// level the sum over at most 4096 contraction indices is below
-// 14 * 225 * 4096 < 2^24 in magnitude, so the FP32 accumulation is exact (an
-// integer).  With kLevelLo = 13 (105 pairs) the dropped levels weigh at most
+// The 105 plane pairs with i + j >= 13 (the 14 most significant weight
+// levels) are multiplied with tcgen05.mma kind::f8f6f4 (e4m3 x e4m3 -> f32)
+// into one TMEM accumulator per level: TMEM region r (32 columns, r = 0..15)
+// holds level r + 11.  The Y planes of one stage lie in shared memory one
+// after the other, so planes j0 .. j0+n-1 form one operand of N = 32 n rows,
+// and one instruction A_i x [Y_j0; ...; Y_j0+n-1] (128 x 32n x 32) adds pair
+// (i, j0 + v) into region i + j0 + v - 11 for v < n.  22 such instructions
+// (N = 32 .. 256) cover the 105 pairs, plus 6 pairs of levels 11 and 12,
+// whose regions are never read.  Per level the sum over at most 4096
+// contraction indices is below 14 * 225 * 4096 < 2^24 in magnitude, so the
+// FP32 accumulation is exact (an integer).  The dropped levels weigh at most
 // about 2^-52.5 of the scales' product per index, so below 2^-50.5 of the
 // product of the two largest magnitudes.
 //
-// Schedule.  A block ((27 - kLevelLo) / 2 warps) computes a 32 x 32 tile of
-// C: warp w owns levels kLevelLo + w and 26 - w (for kLevelLo = 13: 15 plane
-// pairs, equal for every warp); the
-// planes of 32 contraction indices are staged in shared memory by
-// asynchronous copies, two stages deep, so the next stage streams in while
-// the tensor cores work on the current one.  At the end the 14 exact level
-// sums of every element go through shared memory as integers; groups of
-// seven levels are each combined exactly in 64-bit integers (below 2^49) and
-// joined by FP64 fused multiply-adds (one rounding for two groups), so the
-// FP64 pipe does a handful of operations per element.
-// A projection tile is a sub-chunk's partial (a fixed-order sum over
-// sub-chunks gives C); an update tile is subtracted from C.
+// Schedule.  A block of 4 warps computes a 128 x 32 tile of C over its
+// contraction range (a sub-chunk of a projection, all of K for an update).
+// Three shared-memory stages of 70 KiB rotate: one thread issues the bulk
+// copies of a stage (completion counted in bytes on the stage's "full"
+// mbarrier), one thread issues its 22 MMAs and commits them to the stage's
+// "empty" mbarrier, which frees the stage for the copy three stages later.
+// At the end every thread reads the 14 level sums of its row from TMEM,
+// combines levels 13..19 and 20..26 exactly in 64-bit integers (below 2^49),
+// builds the two scaled doubles with integer operations and adds them (one
+// rounding), so the FP64 pipe does one operation per element (two for an
+// update, which subtracts the tile from C).  Every wait is bounded; on
+// expiry the block records CQR_STATUS_TIMEOUT, waits (bounded) for its
+// copies in flight, frees its TMEM and returns.
 #include "cqr_common.cuh"
+#include "cqr.h"
 
 namespace cqr {
 
@@ -47,16 +61,30 @@ constexpr int kSub = 4096;          // rows per sub-chunk (exact FP32 level sums
 constexpr int kPlanes = 14;         // nibbles: 56 bits
 constexpr int kLevelLo = 13;        // lowest weight level i + j kept
 constexpr int kLevels = 2 * kPlanes - 1 - kLevelLo;
-static_assert(kLevels % 2 == 0 && kLevels <= 21, "two levels per warp, at most three groups of seven");
-constexpr int kOzWarps = kLevels / 2;
-constexpr int kOzThreads = 32 * kOzWarps;
-constexpr int kTile = 32;           // output tile (p and q)
-constexpr int kStage = 32;          // rows per shared-memory stage (one k32 MMA step)
-constexpr int kLdk = kStage + 16;   // bytes per column row in shared memory (conflict-free fragments)
-constexpr int kBufBytes = 2 * kPlanes * kTile * kLdk;  // one stage of both operands
+constexpr int kStage = 32;          // contraction indices per stage (one MMA K step for 8-bit types)
 constexpr int kStagesPerSub = kSub / kStage;
 constexpr int kExpZero = -100000;   // scale of an all-zero column
 constexpr int kExpBad = 100000;     // a column holding Inf or NaN
+
+constexpr int kTcM = 128;           // rows of the tile (X side, TMEM lanes)
+constexpr int kTcN = 32;            // columns of the tile (Y side)
+constexpr int kTcThreads = 128;
+constexpr int kTcRing = 3;
+constexpr int kTcABytes = kPlanes * kTcM * kStage;    // 57344
+constexpr int kTcBBytes = kPlanes * kTcN * kStage;    // 14336
+constexpr int kTcStageBytes = kTcABytes + kTcBBytes;  // 71680
+constexpr int kTcSmem = kTcRing * kTcStageBytes + 1024;  // + alignment slack
+constexpr uint32_t kTcCols = 512;   // TMEM columns: 16 regions of kTcN, levels 11..26
+constexpr int kRegionLo = 11;       // level of TMEM region 0
+static_assert((2 * kPlanes - 1 - kRegionLo) * kTcN == (int)kTcCols, "level regions fill the TMEM allocation");
+static_assert(kLevelLo == 13 && kLevels == 14, "the MMA schedule and the two groups of seven levels");
+// Instruction descriptor of tcgen05.mma kind::f8f6f4 without N: D f32 (bits
+// 4-5 = 1), A and B e4m3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 =
+// 0), M >> 4 at bits 24-28; N >> 3 goes to bits 17-22.
+constexpr uint32_t kTcIdescM = (1u << 4) | ((uint32_t)(kTcM >> 4) << 24);
+constexpr long kTcSpin = 1L << 24;  // bound of every mbarrier wait (iterations of try_wait)
+
+inline int round_up(int x, int t) { return (x + t - 1) / t * t; }
 
 // e4m3 codes of 0..15 (exact): 0, 1.0, 2, 3, 4, 5, 6, 7, 8, 9, ..., 15.
 __device__ __forceinline__ uint32_t e4m3_of_nibble(uint32_t n) {
@@ -84,13 +112,18 @@ __device__ __forceinline__ void put_digits(unsigned long long b, int e, uint32_t
   }
 }
 
+// Byte offset, within one (stage, plane) block, of the 16 indices
+// 16*half .. 16*half+15 of column col (canonical K-major layout).
+__device__ __forceinline__ i64 plane_off(i64 col, int half) {
+  return (col >> 3) * 256 + half * 128 + (col & 7) * 16;
+}
+
 // ---------------------------------------------------------------------------
-// Splitting: X (rows r0 .. r0 + nsub*kSub of an m x c matrix) -> planes.
-// Grid (nsub, c); 256 threads; thread t handles rows 16t .. 16t+15 of the
-// sub-chunk as four words of four consecutive rows.
-// planes layout: byte ((s * kStagesPerSub + st) * kPlanes + i) * c * 32 +
-// col * 32 + (row in stage); exps: [s * c + col].
-__global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c,
+// Column splitting: X (rows r0 .. r0 + nsub*kSub of an m x c matrix) ->
+// planes.  Grid (nsub, c); 256 threads; thread t handles rows 16t .. 16t+15
+// of the sub-chunk (half t & 1 of stage t / 2).  Plane block (s, st, i) starts
+// at byte ((s * kStagesPerSub + st) * kPlanes + i) * cp * 32; exps: [s * c + col].
+__global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c, int cp,
                                                           uint8_t* planes, int* exps, const int* status) {
   if (status && *status) return;
   const int s = blockIdx.x, col = blockIdx.y, t = threadIdx.x;
@@ -134,22 +167,21 @@ __global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 l
 #pragma unroll
     for (int k = 0; k < 4; ++k) put_digits(bits[4 * g + k], e, words, g, k);
   }
-  const int st = (16 * t) / kStage, inrow = (16 * t) % kStage;
-  uint8_t* dst = planes + ((i64)s * kStagesPerSub + st) * kPlanes * c * kStage + (i64)col * kStage + inrow;
+  const int st = t >> 1, half = t & 1;
+  uint8_t* dst = planes + ((i64)s * kStagesPerSub + st) * kPlanes * cp * kStage + plane_off(col, half);
 #pragma unroll
   for (int i = 0; i < kPlanes; ++i) {
     uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
-    *reinterpret_cast<uint4*>(dst + (i64)i * c * kStage) = v;
+    *reinterpret_cast<uint4*>(dst + (i64)i * cp * kStage) = v;
   }
 }
 
 // Row splitting for C -= X Y: rows r0 .. r0 + rows of X (m x K, ldx) over the
 // contraction columns k0 .. k0 + kc (kc <= kSub).  Thread = row; every row
 // gets its own scale over its kc entries (first pass), then its digits for
-// 16 columns at a time (second pass) go to byte ((st * kPlanes + i) * rows +
-// row) * 32 + (k - k0) % 32 with st = (k - k0) / 32: the column layout above
-// with rows in the role of columns.  rows is a multiple of 32; rows at or
-// past m split as zeros.
+// 16 columns at a time (second pass) go to plane block (st, i) at byte
+// (st * kPlanes + i) * rows * 32, rows in the role of columns.  rows is a
+// multiple of the tile height; rows at or past m split as zeros.
 __global__ void __launch_bounds__(128) ozaki_rowsplit_kernel(const double* X, i64 ldx, i64 m, i64 r0, int rows,
                                                              i64 k0, int kc, uint8_t* planes, int* exps,
                                                              const int* status) {
@@ -189,7 +221,7 @@ __global__ void __launch_bounds__(128) ozaki_rowsplit_kernel(const double* X, i6
           put_digits((unsigned long long)__double_as_longlong(v), e, words, g, k);
         }
       }
-      uint8_t* dst = planes + ((i64)st * kPlanes * rows + row) * kStage + 16 * h;
+      uint8_t* dst = planes + (i64)st * kPlanes * rows * kStage + plane_off(row, h);
 #pragma unroll
       for (int i = 0; i < kPlanes; ++i) {
         uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
@@ -199,191 +231,273 @@ __global__ void __launch_bounds__(128) ozaki_rowsplit_kernel(const double* X, i6
   }
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_e4m3(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 // ---------------------------------------------------------------------------
-// One 32 x 32 tile of C.  Projection (NN = false): grid (nsub, tiles_p,
-// tiles_q), the tile of sub-chunk s goes to the partial buffer.  Update
-// (NN = true): one launch per chunk of rows, a linear grid with the q tile
-// fastest (the blocks of one row tile run together and share its X planes
-// in L2), and C -= tile.
+// tcgen05, TMEM, bulk copies and mbarriers (inline PTX).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: canonical K-major layout without
+// swizzling; leading (K-direction) core-matrix offset 128 bytes, stride
+// between 8-row groups 256 bytes; version 1 (bit 46).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait; false when the bound expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long it = 0; it < kTcSpin; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// D (TMEM) += A x B^T with N = 32 * nb (accumulating: the regions start zeroed)
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t ad, uint64_t bd, int nb) {
+  const uint32_t idesc = kTcIdescM | ((uint32_t)(kTcN * nb >> 3) << 17);
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc));
+}
+// zeros into 32 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_st_zero32(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// The MMA schedule of one stage: (plane i of X, first plane j0 of Y, count n).
+struct TcMma {
+  int i, j0, n;
+};
+__device__ constexpr TcMma kTcSchedule[22] = {
+    {11, 0, 8}, {12, 0, 8}, {13, 0, 8},                                  // i >= 11 with all of j = 0..7
+    {3, 8, 6},  {4, 8, 6},  {5, 8, 6},  {6, 8, 6},  {7, 8, 6}, {8, 8, 6},  // j = 8..13 for i >= 3
+    {9, 8, 6},  {10, 8, 6}, {11, 8, 6}, {12, 8, 6}, {13, 8, 6},
+    {6, 7, 1},  {7, 6, 2},  {8, 5, 3},  {9, 4, 4},  {10, 3, 5},            // j <= 7 with i + j >= 13, i <= 10
+    {2, 11, 3}, {1, 12, 2}, {0, 13, 1}};                                 // j >= 11 with i + j >= 13, i <= 2
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 8 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// g * 2^e for an integer |g| < 2^53 (exact), built with integer operations;
+// outside the normal range it falls back to the FP64 library ldexp.
+__device__ __forceinline__ double scaled_int(long long g, int e) {
+  if (g == 0) return 0.0;
+  const unsigned long long sgn = g < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = g < 0 ? (unsigned long long)(-g) : (unsigned long long)g;
+  const int msb = 63 - __clzll((long long)a);
+  const int E = msb + e + 1023;
+  if (E <= 0 || E >= 2047) return ldexp((double)g, e);
+  const unsigned long long mant = (a << (52 - msb)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | mant));
+}
+
 struct OzArgs {
-  const uint8_t* px;  // planes of X (projection: p columns; update: p rows)
-  const uint8_t* py;  // planes of Y (q columns)
+  const uint8_t* px;  // planes of X (the tile's rows: projection columns p / update rows)
+  const uint8_t* py;  // planes of Y (the tile's columns q)
   const int* ex;
   const int* ey;
-  int p, q;
+  int p, q;           // extents (projection: p x q; update: rows of the chunk x N)
+  int cpx, cpy;       // padded column counts of the plane blocks
+  int nst;            // stages per tile (projection: kStagesPerSub)
+  int tiles_q;
   int s_off;          // projection: sub-chunk index offset of this launch in the partial buffer
   double* part;       // projection: [s][p * q] column-major p x q
-  int nst;            // update: stages of 32 contraction indices
-  int tiles_q;        // update: ceil(q / 32)
-  int p_live;         // update: rows of the chunk that exist (p rounded up to 32 is the planes' row count)
   double* C;          // update: C (ldc) of the chunk's first row
   i64 ldc;
-  const int* status;
+  int* status;
 };
 
-constexpr int kLvlLd = kTile + 4;  // level-sum staging: column stride in ints (conflict-free writes)
-
+// One 128 x 32 tile.  Projection (NN = false): grid (tiles_q, tiles_p, nsub),
+// the tile of sub-chunk s goes to the partial buffer.  Update (NN = true):
+// a linear grid with the q tile fastest (the blocks of one row tile run
+// together and share its X planes in L2), and C -= tile.
 template <bool NN>
-__global__ void __launch_bounds__(kOzThreads, 2) ozaki_kernel(OzArgs a) {
-  extern __shared__ __align__(16) uint8_t osm[];
-  if (a.status && *a.status) return;
-  int s, p0, q0, nst;
+__global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
+  extern __shared__ uint8_t tc_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kTcRing], empty_bar[kTcRing], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int give_up;
+  if (a.status && *a.status) return;  // uniform across the block, before any allocation
+  int s, p0, q0;
   if (NN) {
     s = 0;
-    q0 = (int)(blockIdx.x % (unsigned)a.tiles_q) * kTile;
-    p0 = (int)(blockIdx.x / (unsigned)a.tiles_q) * kTile;
-    nst = a.nst;
+    q0 = (int)(blockIdx.x % (unsigned)a.tiles_q) * kTcN;
+    p0 = (int)(blockIdx.x / (unsigned)a.tiles_q) * kTcM;
   } else {
-    s = blockIdx.x;
-    p0 = blockIdx.y * kTile;
-    q0 = blockIdx.z * kTile;
-    nst = kStagesPerSub;
+    q0 = blockIdx.x * kTcN;
+    p0 = blockIdx.y * kTcM;
+    s = blockIdx.z;
   }
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int g = lane >> 2, tq = lane & 3;
-  const int lvA = kLevelLo + warp, lvB = 2 * kPlanes - 2 - warp;  // weight levels i + j of this warp
-  float accA[2][4][4], accB[2][4][4];
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) accA[mi][ni][r] = accB[mi][ni][r] = 0.f;
-
-  // Copy plan of one stage: 2 operands x 14 planes x 32 columns x 32 bytes =
-  // 1792 pieces of 16 bytes, the same number per thread; the offsets are
-  // recomputed per stage, which costs a few integer operations and keeps the
-  // registers for the accumulators.
-  constexpr int kPieces = 2 * kPlanes * kTile * (kStage / 16);
-  constexpr int kPer = kPieces / kOzThreads;
-  static_assert(kPieces % kOzThreads == 0, "copy plan");
-  const i64 stage_x = (i64)kPlanes * a.p * kStage, stage_y = (i64)kPlanes * a.q * kStage;
-  const uint8_t* bx = a.px + (i64)s * kStagesPerSub * stage_x;
-  const uint8_t* by = a.py + (i64)s * kStagesPerSub * stage_y;
-  auto issue = [&](int st, uint8_t* buf) {
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int e = t + kOzThreads * k;
-      const int op = e >= kPieces / 2 ? 1 : 0;
-      const int r = e - op * (kPieces / 2);
-      const int pl = r / (kTile * 2), within = r % (kTile * 2);
-      const int colp = within >> 1, piece = within & 1;
-      const int c = op == 0 ? a.p : a.q;
-      const int colg = (op == 0 ? p0 : q0) + colp;
-      const bool ok = colg < c;  // zero fill beyond the last column; offsets < 14 * c * 32 < 2^31
-      const uint8_t* src = (op == 0 ? bx + st * stage_x : by + st * stage_y) +
-                           (ok ? pl * c * kStage + colg * kStage + 16 * piece : 0);
-      cp_async16(buf + (op * kPlanes * kTile + pl * kTile + colp) * kLdk + 16 * piece, src, ok ? 16 : 0);
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+  if (t == 0) {
+    for (int i = 0; i < kTcRing; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), 1);
     }
-  };
-  issue(0, osm);
-  cp_async_commit();
-  for (int st = 0; st < nst; ++st) {
-    if (st + 1 < nst) issue(st + 1, osm + ((st + 1) & 1) * kBufBytes);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    const uint8_t* sx = osm + (st & 1) * kBufBytes + (16 * 0 + g) * kLdk + 4 * tq;   // + (i*kTile + 16 mi) * kLdk
-    const uint8_t* sy = osm + (st & 1) * kBufBytes + (kPlanes * kTile + g) * kLdk + 4 * tq;
-    // plane i of X against planes j = lvA - i and lvB - i of Y (warp-uniform predicates)
-#pragma unroll
-    for (int i = 0; i < kPlanes; ++i) {
-      const int jA = lvA - i, jB = lvB - i;
-      const bool useA = jA >= 0 && jA < kPlanes, useB = jB >= 0 && jB < kPlanes;
-      if (useA || useB) {
-        uint32_t af[2][4];
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          const uint8_t* base = sx + (i * kTile + 16 * mi) * kLdk;
-          af[mi][0] = *reinterpret_cast<const uint32_t*>(base);
-          af[mi][1] = *reinterpret_cast<const uint32_t*>(base + 8 * kLdk);
-          af[mi][2] = *reinterpret_cast<const uint32_t*>(base + 16);
-          af[mi][3] = *reinterpret_cast<const uint32_t*>(base + 8 * kLdk + 16);
-        }
-        if (useA) {
-#pragma unroll
-          for (int ni = 0; ni < 4; ++ni) {
-            const uint8_t* bb = sy + (jA * kTile + 8 * ni) * kLdk;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bb);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bb + 16);
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) mma_e4m3(accA[mi][ni], af[mi][0], af[mi][1], af[mi][2], af[mi][3], b0, b1);
-          }
-        }
-        if (useB) {
-#pragma unroll
-          for (int ni = 0; ni < 4; ++ni) {
-            const uint8_t* bb = sy + (jB * kTile + 8 * ni) * kLdk;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bb);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bb + 16);
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) mma_e4m3(accB[mi][ni], af[mi][0], af[mi][1], af[mi][2], af[mi][3], b0, b1);
-          }
-        }
-      }
-    }
-    __syncthreads();  // the buffer is refilled two stages later
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    give_up = 0;
   }
-  // the level sums are exact integers below 2^24: stage them as int32,
-  // [level - 13][col * kLvlLd + row]
-  int* lvl = reinterpret_cast<int*>(osm);
-  constexpr int kLvlStride = kTile * kLvlLd;
-#pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int row = 16 * mi + g + (r >= 2 ? 8 : 0);  // p index in tile
-        const int col = 8 * ni + 2 * tq + (r & 1);       // q index in tile
-        lvl[(lvA - kLevelLo) * kLvlStride + col * kLvlLd + row] = __float2int_rz(accA[mi][ni][r]);
-        lvl[(lvB - kLevelLo) * kLvlStride + col * kLvlLd + row] = __float2int_rz(accB[mi][ni][r]);
-      }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
   __syncthreads();
-  const int p_end = NN ? a.p_live : a.p;
-  for (int e = t; e < kTile * kTile; e += kOzThreads) {
-    const int row = e % kTile, col = e / kTile;
-    const int pr = p0 + row, qc = q0 + col;
-    if (pr >= p_end || qc >= a.q) continue;
-    // sum_L S_L 16^L = 16^kLevelLo (g0 + 2^28 g1 + 2^56 g2), group g_i = sum of
-    // S_L 16^(L - kLevelLo - 7 i) over its (at most seven) levels
-    const int* le = lvl + col * kLvlLd + row;
-    long long grp[3] = {0, 0, 0};
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  // every MMA accumulates: zero the 16 level regions (each warp its 32 lanes)
+  for (int c = 0; c < (int)kTcCols; c += 32) tc_st_zero32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c);
+  tc_wait_st();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const int nst = a.nst;
+  const i64 stage_x = (i64)kPlanes * a.cpx * kStage, stage_y = (i64)kPlanes * a.cpy * kStage;
+  const uint8_t* gx = a.px + (i64)s * kStagesPerSub * stage_x + (i64)p0 * kStage;
+  const uint8_t* gy = a.py + (i64)s * kStagesPerSub * stage_y + (i64)q0 * kStage;
+
+  if (warp == 0 && lane == 0) {
+    // producer: bulk copies of stage st into ring slot st % kTcRing
+    int issued = 0;
+    for (int st = 0; st < nst; ++st) {
+      const int slot = st % kTcRing;
+      if (st >= kTcRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((st / kTcRing - 1) & 1))) {
+        atomicExch(&give_up, 1);
+        break;
+      }
+      if (*(volatile int*)&give_up) break;
+      const uint32_t fb = smem_u32(&full_bar[slot]);
+      const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
+      mbar_expect_tx(fb, kTcStageBytes);
+      const uint8_t* xs = gx + st * stage_x;
+      const uint8_t* ys = gy + st * stage_y;
+#pragma unroll 1
+      for (int i = 0; i < kPlanes; ++i) {
+        bulk_g2s(sa + i * (kTcM * kStage), xs + (i64)i * a.cpx * kStage, kTcM * kStage, fb);
+        bulk_g2s(sb + i * (kTcN * kStage), ys + (i64)i * a.cpy * kStage, kTcN * kStage, fb);
+      }
+      issued = st + 1;
+    }
+    // before leaving, every issued copy must have landed (bounded)
+    for (int st = issued - kTcRing < 0 ? 0 : issued - kTcRing; st < issued; ++st)
+      mbar_wait(smem_u32(&full_bar[st % kTcRing]), (uint32_t)((st / kTcRing) & 1));
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: the 22 instructions of each stage (the 105 pairs, level L = i + j into region L - 11)
+    for (int st = 0; st < nst; ++st) {
+      const int slot = st % kTcRing;
+      if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((st / kTcRing) & 1))) {
+        atomicExch(&give_up, 1);
+        break;
+      }
+      if (*(volatile int*)&give_up) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
+      const uint64_t ad0 = tc_desc(sa), bd0 = tc_desc(sb);
 #pragma unroll
-    for (int L = kLevels - 1; L >= 0; --L) grp[L / 7] = grp[L / 7] * 16 + le[L * kLvlStride];
-    // |g_i| < 2^49: exact operands; one rounding per fused multiply-add
-    const double v = fma((double)grp[2], 72057594037927936.0, fma((double)grp[1], 268435456.0, (double)grp[0]));
-    const int ex = a.ex[(i64)s * a.p + pr], ey = a.ey[(i64)s * a.q + qc];
-    double scale;
-    if (ex == kExpBad || ey == kExpBad)
-      scale = __longlong_as_double(0x7ff8000000000000LL);
-    else if (ex == kExpZero || ey == kExpZero)
-      scale = 0.0;
-    else
-      scale = ldexp(1.0, ex + ey - 112 + 4 * kLevelLo);
-    if (NN) {
-      double* cp = a.C + pr + (i64)qc * a.ldc;
-      *cp -= v * scale;
-    } else {
-      a.part[(i64)(a.s_off + s) * a.p * a.q + pr + (i64)qc * a.p] = v * scale;
+      for (int u = 0; u < 22; ++u) {
+        const TcMma e = kTcSchedule[u];
+        const uint64_t ad = ad0 + (uint64_t)((e.i * kTcM * kStage) >> 4);
+        const uint64_t bd = bd0 + (uint64_t)((e.j0 * kTcN * kStage) >> 4);
+        tc_mma(tmem + (uint32_t)((e.i + e.j0 - kRegionLo) * kTcN), ad, bd, e.n);
+      }
+      tc_commit(smem_u32(&empty_bar[slot]));
+    }
+    tc_commit(smem_u32(&done_bar));  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+  const bool done = mbar_wait(smem_u32(&done_bar), 0);
+  // one decision for the whole block, and converged warps for tcgen05.ld
+  const int failed = __syncthreads_or(!done || *(volatile int*)&give_up);
+  tc_fence_after();
+  if (failed) {
+    if (t == 0 && a.status) atomicCAS(a.status, 0, CQR_STATUS_TIMEOUT);
+  } else {
+    // epilogue: row r of the tile (TMEM lane r), 8 columns at a time
+    const int r = 32 * warp + lane;
+    const int pr = p0 + r;
+    const bool live = pr < a.p;
+    const int exr = live ? a.ex[(i64)s * a.p + pr] : kExpZero;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTcN; c0 += 8) {
+      long long g[2][8];
+#pragma unroll
+      for (int grp = 1; grp >= 0; --grp) {
+        uint32_t v[7][8];
+#pragma unroll
+        for (int l = 6; l >= 0; --l)
+          tc_ld8(lane_base + (uint32_t)((kLevelLo - kRegionLo + 7 * grp + l) * kTcN + c0), v[l]);
+        tc_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          long long acc = 0;
+#pragma unroll
+          for (int l = 6; l >= 0; --l) acc = acc * 16 + __float2int_rz(__uint_as_float(v[l][j]));
+          g[grp][j] = acc;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int qc = q0 + c0 + j;
+        if (!live || qc >= a.q) continue;
+        const int eyc = a.ey[(i64)s * a.q + qc];
+        double v;
+        if (exr == kExpBad || eyc == kExpBad) {
+          v = __longlong_as_double(0x7ff8000000000000LL);
+        } else if (exr == kExpZero || eyc == kExpZero) {
+          v = 0.0;
+        } else {
+          // sum_L S_L 16^L = 16^13 (g0 + 2^28 g1); value = that * 2^(ex + ey - 112)
+          const int e2 = exr + eyc - 112 + 4 * kLevelLo;
+          v = scaled_int(g[1][j], e2 + 28) + scaled_int(g[0][j], e2);  // one rounding
+        }
+        if (NN) {
+          double* cp = a.C + pr + (i64)qc * a.ldc;
+          *cp -= v;
+        } else {
+          a.part[(i64)(a.s_off + s) * a.p * a.q + pr + (i64)qc * a.p] = v;
+        }
+      }
     }
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
 __global__ void ozaki_reduce_kernel(const double* part, i64 nsub, int p, int q, double* C, i64 ldc,
@@ -397,37 +511,41 @@ __global__ void ozaki_reduce_kernel(const double* part, i64 nsub, int p, int q, 
   C[r + (i64)c * ldc] = s;
 }
 
-inline size_t oz_smem() {
-  const size_t planes = (size_t)2 * kBufBytes;
-  const size_t lv = sizeof(int) * kLevels * kTile * kLvlLd;
-  return planes > lv ? planes : lv;
+template <bool NN>
+void tc_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(ozaki_tc_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    done = true;
+  }
 }
 
 // Rows per update chunk: the X planes of one chunk take about 1 GiB.
 inline i64 oz_nn_rows(int nst) {
   i64 rows = ((i64)1 << 30) / ((i64)kPlanes * kStage * nst);
-  rows = rows / kTile * kTile;
-  return rows < kTile ? kTile : rows;
+  rows = rows / kTcM * kTcM;
+  return rows < kTcM ? kTcM : rows;
 }
 
 }  // namespace
 
-// Rows per splitting chunk: planes of one chunk take about 1 GiB.
+// Rows per splitting chunk of a projection: planes of one chunk take about 1 GiB.
 i64 oz_chunk_rows(int p, int q) {
-  i64 rows = ((i64)1 << 30) / ((i64)kPlanes * (p + q));
+  i64 rows = ((i64)1 << 30) / ((i64)kPlanes * (round_up(p, kTcM) + round_up(q, kTcN)));
   rows = (rows / kSub) * kSub;
   return rows < kSub ? kSub : rows;
 }
 
 size_t ozaki_workspace_bytes(i64 m, int p, int q) {
   if (m <= 0 || p <= 0 || q <= 0) return 0;
+  const int cpx = round_up(p, kTcM), cpy = round_up(q, kTcN);
   const i64 nsub_total = (m + kSub - 1) / kSub;
   i64 ch = oz_chunk_rows(p, q);
-  const i64 mr = ((m + kSub - 1) / kSub) * kSub;
+  const i64 mr = nsub_total * kSub;
   if (ch > mr) ch = mr;
   const i64 nsub_ch = ch / kSub;
   size_t b = 0;
-  b += (size_t)nsub_ch * kPlanes * (p + q) * kSub;           // planes of one chunk
+  b += (size_t)nsub_ch * kPlanes * (cpx + cpy) * kSub;        // planes of one chunk
   b = (b + 255) & ~(size_t)255;
   b += sizeof(int) * (size_t)nsub_ch * (p + q);               // scales
   b = (b + 255) & ~(size_t)255;
@@ -438,34 +556,32 @@ size_t ozaki_workspace_bytes(i64 m, int p, int q) {
 cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, const double* Y, i64 ldy,
                                 void* ws, double* C, i64 ldc, const int* status, cudaStream_t st) {
   if (p <= 0 || q <= 0) return cudaSuccess;
+  const int cpx = round_up(p, kTcM), cpy = round_up(q, kTcN);
   const i64 nsub_total = (m + kSub - 1) / kSub;
   i64 ch = oz_chunk_rows(p, q);
   const i64 mr = nsub_total * kSub;
   if (ch > mr) ch = mr;
   const i64 nsub_ch = ch / kSub;
   uint8_t* planes = (uint8_t*)ws;
-  size_t off = (size_t)nsub_ch * kPlanes * (p + q) * kSub;
+  size_t off = (size_t)nsub_ch * kPlanes * (cpx + cpy) * kSub;
   off = (off + 255) & ~(size_t)255;
   int* exps = (int*)((char*)ws + off);
   off += sizeof(int) * (size_t)nsub_ch * (p + q);
   off = (off + 255) & ~(size_t)255;
   double* part = (double*)((char*)ws + off);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(ozaki_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
-    attr = true;
-  }
+  tc_attr<false>();
   uint8_t* px = planes;
-  uint8_t* py = planes + (size_t)nsub_ch * kPlanes * p * kSub;
+  uint8_t* py = planes + (size_t)nsub_ch * kPlanes * cpx * kSub;
   int* ex = exps;
   int* ey = exps + nsub_ch * p;
+  const int tiles_p = cpx / kTcM, tiles_q = cpy / kTcN;
   for (i64 r0 = 0; r0 < m; r0 += ch) {
     const i64 nsub = ((m - r0 < ch ? m - r0 : ch) + kSub - 1) / kSub;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)p), 256, 0, st>>>(X, ldx, m, r0, p, px, ex, status);
+    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)p), 256, 0, st>>>(X, ldx, m, r0, p, cpx, px, ex, status);
     prof_end(kMisc, 0.0, st);
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)q), 256, 0, st>>>(Y, ldy, m, r0, q, py, ey, status);
+    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)q), 256, 0, st>>>(Y, ldy, m, r0, q, cpy, py, ey, status);
     prof_end(kMisc, 0.0, st);
     OzArgs a{};
     a.px = px;
@@ -474,12 +590,15 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
     a.ey = ey;
     a.p = p;
     a.q = q;
+    a.cpx = cpx;
+    a.cpy = cpy;
+    a.nst = kStagesPerSub;
+    a.tiles_q = tiles_q;
     a.s_off = (int)(r0 / kSub);
     a.part = part;
-    a.status = status;
-    dim3 grid((unsigned)nsub, (unsigned)((p + kTile - 1) / kTile), (unsigned)((q + kTile - 1) / kTile));
+    a.status = const_cast<int*>(status);
     prof_begin(kProjection, st);
-    ozaki_kernel<false><<<grid, kOzThreads, oz_smem(), st>>>(a);
+    ozaki_tc_kernel<false><<<dim3((unsigned)tiles_q, (unsigned)tiles_p, (unsigned)nsub), kTcThreads, kTcSmem, st>>>(a);
     prof_end(kProjection, 2.0 * (double)(nsub * kSub < m - r0 ? nsub * kSub : m - r0) * p * q, st);
   }
   const i64 pq = (i64)p * q;
@@ -493,12 +612,13 @@ size_t ozaki_nn_workspace_bytes(i64 M, int N, int K) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
   const int kc = K < kSub ? K : kSub;
   const int nst = (kc + kStage - 1) / kStage;
+  const int cpy = round_up(N, kTcN);
   i64 rows = oz_nn_rows(nst);
-  const i64 mr = (M + kTile - 1) / kTile * kTile;
+  const i64 mr = (M + kTcM - 1) / kTcM * kTcM;
   if (rows > mr) rows = mr;
   size_t b = (size_t)rows * nst * kStage * kPlanes;  // X planes of one chunk
   b = (b + 255) & ~(size_t)255;
-  b += (size_t)kSub * kPlanes * N;                   // Y planes (one sub-chunk)
+  b += (size_t)kSub * kPlanes * cpy;                 // Y planes (one sub-chunk)
   b = (b + 255) & ~(size_t)255;
   b += sizeof(int) * ((size_t)rows + N);             // scales
   return (b + 255) & ~(size_t)255;
@@ -509,49 +629,46 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   const int kcmax = K < kSub ? K : kSub;
   const int nstmax = (kcmax + kStage - 1) / kStage;
+  const int cpy = round_up(N, kTcN);
   i64 rows = oz_nn_rows(nstmax);
-  const i64 mr = (M + kTile - 1) / kTile * kTile;
+  const i64 mr = (M + kTcM - 1) / kTcM * kTcM;
   if (rows > mr) rows = mr;
   uint8_t* px = (uint8_t*)ws;
   size_t off = ((size_t)rows * nstmax * kStage * kPlanes + 255) & ~(size_t)255;
   uint8_t* py = (uint8_t*)ws + off;
-  off = (off + (size_t)kSub * kPlanes * N + 255) & ~(size_t)255;
+  off = (off + (size_t)kSub * kPlanes * cpy + 255) & ~(size_t)255;
   int* ex = (int*)((char*)ws + off);
   int* ey = ex + rows;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(ozaki_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem());
-    attr = true;
-  }
-  const int tiles_q = (N + kTile - 1) / kTile;
+  tc_attr<true>();
+  const int tiles_q = cpy / kTcN;
   for (i64 k0 = 0; k0 < K; k0 += kSub) {
     const int kc = (int)(K - k0 < kSub ? K - k0 : kSub);
     const int nst = (kc + kStage - 1) / kStage;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3(1u, (unsigned)N), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, py, ey, status);
+    ozaki_split_kernel<<<dim3(1u, (unsigned)N), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, cpy, py, ey, status);
     prof_end(kMisc, 0.0, st);
     for (i64 r0 = 0; r0 < M; r0 += rows) {
       const i64 live = M - r0 < rows ? M - r0 : rows;
-      const int rws = (int)((live + kTile - 1) / kTile * kTile);
+      const int rws = (int)((live + kTcM - 1) / kTcM * kTcM);
       prof_begin(kMisc, st);
-      ozaki_rowsplit_kernel<<<(unsigned)((rws + 127) / 128), 128, 0, st>>>(X, ldx, M, r0, rws, k0, kc, px, ex,
-                                                                          status);
+      ozaki_rowsplit_kernel<<<(unsigned)(rws / 128), 128, 0, st>>>(X, ldx, M, r0, rws, k0, kc, px, ex, status);
       prof_end(kMisc, 0.0, st);
       OzArgs a{};
       a.px = px;
       a.py = py;
       a.ex = ex;
       a.ey = ey;
-      a.p = rws;
+      a.p = (int)live;
       a.q = N;
+      a.cpx = rws;
+      a.cpy = cpy;
       a.nst = nst;
       a.tiles_q = tiles_q;
-      a.p_live = (int)live;
       a.C = C + r0;
       a.ldc = ldc;
-      a.status = status;
+      a.status = const_cast<int*>(status);
       prof_begin(kUpdate, st);
-      ozaki_kernel<true><<<(unsigned)((i64)(rws / kTile) * tiles_q), kOzThreads, oz_smem(), st>>>(a);
+      ozaki_tc_kernel<true><<<(unsigned)((i64)(rws / kTcM) * tiles_q), kTcThreads, kTcSmem, st>>>(a);
       prof_end(kUpdate, 2.0 * (double)live * N * kc, st);
     }
   }
