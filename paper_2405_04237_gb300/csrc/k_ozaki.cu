@@ -14,13 +14,14 @@
 // own scale over (at most kSub of) its entries and takes a column's place;
 // Y (K x N) is split by columns.
 //
-// Plane layout.  One "stage" is 32 contraction indices.  For stage st and
-// plane i the digits of all columns form one block of cp * 32 bytes (cp =
-// the column count rounded up to the tile), in the tensor cores' canonical
-// K-major layout without swizzling: 8-column groups of 256 bytes, each two
-// 8 x 16-byte core matrices (indices 0..15, then 16..31).  A 128-column tile
-// of one plane is thus one contiguous 4 KiB run and a 32-column tile one
-// 1 KiB run, which the kernel fetches with plain bulk asynchronous copies.
+// Plane layout.  One "stage" is 32 contraction indices.  Columns are grouped
+// in tiles of T (128 on the X side, 32 on the Y side), and the planes are
+// stored tile-major: for each tile, each stage, each plane i, the T x 32
+// digits in the tensor cores' canonical K-major layout without swizzling
+// (8-column groups of 256 bytes, each two 8 x 16-byte core matrices holding
+// indices 0..15, then 16..31).  The 14 planes of one stage of one tile are
+// thus one contiguous run (56 KiB for X, 14 KiB for Y), and a stage arrives
+// in shared memory with two bulk asynchronous copies.
 //
 // Products.  x_a y_b = 2^(e_a + e_b - 112) sum_{i,j} d^x_i d^y_j 16^(i+j).
 // The 105 plane pairs with i + j >= 13 (the 14 most significant weight
@@ -86,29 +87,51 @@ constexpr long kTcSpin = 1L << 24;  // bound of every mbarrier wait (iterations 
 
 inline int round_up(int x, int t) { return (x + t - 1) / t * t; }
 
-// e4m3 codes of 0..15 (exact): 0, 1.0, 2, 3, 4, 5, 6, 7, 8, 9, ..., 15.
-__device__ __forceinline__ uint32_t e4m3_of_nibble(uint32_t n) {
-  // bytes for 0..7 from two lookup words, 8..15 are 0x48 + n (linear)
-  const uint32_t lo = __byte_perm(0x44403800u, 0x4E4C4A48u, n & 7u);
-  return n < 8 ? (lo & 0xFFu) : (0x48u + n);
+// 56-bit magnitude |x| * 2^(56 - e) (truncated) of one FP64 value (raw bits b)
+// against scale e; zero for zeros, subnormals and a bad column.
+__device__ __forceinline__ unsigned long long magnitude(unsigned long long b, int e) {
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF || e == kExpBad) return 0ull;
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1019 - e;  // |x| 2^(56-e) = M 2^(E - 1075 + 56 - e)
+  return sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
 }
 
-// Digits of one FP64 value (raw bits b) against scale e into byte k of
-// word g of the 14 plane words.
-__device__ __forceinline__ void put_digits(unsigned long long b, int e, uint32_t (&words)[kPlanes][4], int g, int k) {
-  const int E = (int)((b >> 52) & 0x7FF);
-  unsigned long long mag = 0ull;
-  if (E != 0 && E != 0x7FF && e != kExpBad) {
-    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - 1019 - e;  // |x| 2^(56-e) = M 2^(E - 1075 + 56 - e)
-    mag = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
-  }
-  const uint32_t sign = (uint32_t)(b >> 63) << 7;
+// e4m3 codes of four nibbles (one per byte of n, each 0..15): 0, 1, ..., 7
+// come from two lookup words, 8..15 (0x50 + n - 8) from two more, chosen per
+// byte by bit 3 of the nibble.
+__device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t n) {
+  const uint32_t v = n & 0x07070707u;
+  const uint32_t u = v | (v >> 4);
+  const uint32_t sel = __byte_perm(u, 0u, 0x4420);  // selector nibbles v0, v1, v2, v3
+  const uint32_t lo = __byte_perm(0x44403800u, 0x4E4C4A48u, sel);
+  const uint32_t hi = __byte_perm(0x53525150u, 0x57565554u, sel);
+  const uint32_t mask = ((n >> 3) & 0x01010101u) * 0xFFu;
+  return (lo & ~mask) | (hi & mask);
+}
+
+// Digits of four FP64 values (raw bits b[0..3]) against scale e: byte k of
+// word i is the e4m3 code of digit i of value k, sign(x_k) * nibble i.  The
+// four 56-bit magnitudes are transposed bytewise with byte permutes, so that
+// every step below works on four values at once.
+__device__ __forceinline__ void digits4(const unsigned long long (&b)[4], int e, uint32_t (&w)[kPlanes]) {
+  uint32_t lo[4], hi[4], sgn = 0;
 #pragma unroll
-  for (int i = 0; i < kPlanes; ++i) {
-    const uint32_t n = (uint32_t)(mag >> (4 * i)) & 15u;
-    const uint32_t code = n ? (e4m3_of_nibble(n) | sign) : 0u;
-    words[i][g] |= code << (8 * k);
+  for (int k = 0; k < 4; ++k) {
+    const unsigned long long m = magnitude(b[k], e);
+    lo[k] = (uint32_t)m;
+    hi[k] = (uint32_t)(m >> 32);
+    sgn |= (uint32_t)(b[k] >> 63) << (8 * k + 7);
+  }
+#pragma unroll
+  for (int j = 0; j < kPlanes / 2; ++j) {  // byte j of the four magnitudes
+    const uint32_t* src = j < 4 ? lo : hi;
+    const uint32_t sel = (uint32_t)(j & 3) | ((uint32_t)((j & 3) + 4) << 4);
+    const uint32_t t01 = __byte_perm(src[0], src[1], sel);
+    const uint32_t t23 = __byte_perm(src[2], src[3], sel);
+    const uint32_t bj = __byte_perm(t01, t23, 0x5410);
+    w[2 * j] = e4m3_of_nibbles(bj & 0x0F0F0F0Fu) | sgn;
+    w[2 * j + 1] = e4m3_of_nibbles((bj >> 4) & 0x0F0F0F0Fu) | sgn;
   }
 }
 
@@ -121,9 +144,11 @@ __device__ __forceinline__ i64 plane_off(i64 col, int half) {
 // ---------------------------------------------------------------------------
 // Column splitting: X (rows r0 .. r0 + nsub*kSub of an m x c matrix) ->
 // planes.  Grid (nsub, c); 256 threads; thread t handles rows 16t .. 16t+15
-// of the sub-chunk (half t & 1 of stage t / 2).  Plane block (s, st, i) starts
-// at byte ((s * kStagesPerSub + st) * kPlanes + i) * cp * 32; exps: [s * c + col].
-__global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c, int cp,
+// of the sub-chunk (half t & 1 of stage t / 2).  Tiles of T columns; plane
+// block (s, tile, st, i) starts at byte
+// (((s * ntile + tile) * kStagesPerSub + st) * kPlanes + i) * T * 32 with
+// ntile = ceil(c / T); exps: [s * c + col].
+__global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c, int T,
                                                           uint8_t* planes, int* exps, const int* status) {
   if (status && *status) return;
   const int s = blockIdx.x, col = blockIdx.y, t = threadIdx.x;
@@ -162,26 +187,30 @@ __global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 l
   uint32_t words[kPlanes][4];
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
+    const unsigned long long b4[4] = {bits[4 * g], bits[4 * g + 1], bits[4 * g + 2], bits[4 * g + 3]};
+    uint32_t w[kPlanes];
+    digits4(b4, e, w);
 #pragma unroll
-    for (int i = 0; i < kPlanes; ++i) words[i][g] = 0u;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) put_digits(bits[4 * g + k], e, words, g, k);
+    for (int i = 0; i < kPlanes; ++i) words[i][g] = w[i];
   }
   const int st = t >> 1, half = t & 1;
-  uint8_t* dst = planes + ((i64)s * kStagesPerSub + st) * kPlanes * cp * kStage + plane_off(col, half);
+  const int ntile = (c + T - 1) / T;
+  uint8_t* dst = planes + (((i64)s * ntile + col / T) * kStagesPerSub + st) * kPlanes * T * kStage +
+                 plane_off(col % T, half);
 #pragma unroll
   for (int i = 0; i < kPlanes; ++i) {
     uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
-    *reinterpret_cast<uint4*>(dst + (i64)i * cp * kStage) = v;
+    *reinterpret_cast<uint4*>(dst + (i64)i * T * kStage) = v;
   }
 }
 
 // Row splitting for C -= X Y: rows r0 .. r0 + rows of X (m x K, ldx) over the
 // contraction columns k0 .. k0 + kc (kc <= kSub).  Thread = row; every row
 // gets its own scale over its kc entries (first pass), then its digits for
-// 16 columns at a time (second pass) go to plane block (st, i) at byte
-// (st * kPlanes + i) * rows * 32, rows in the role of columns.  rows is a
-// multiple of the tile height; rows at or past m split as zeros.
+// 16 columns at a time (second pass) go to plane block (tile, st, i) at
+// byte ((tile * nst + st) * kPlanes + i) * 128 * 32 with tile = row / 128,
+// rows in the role of columns.  rows is a multiple of 128; rows at or past m
+// split as zeros.
 __global__ void __launch_bounds__(128) ozaki_rowsplit_kernel(const double* X, i64 ldx, i64 m, i64 r0, int rows,
                                                              i64 k0, int kc, uint8_t* planes, int* exps,
                                                              const int* status) {
@@ -212,20 +241,22 @@ __global__ void __launch_bounds__(128) ozaki_rowsplit_kernel(const double* X, i6
       uint32_t words[kPlanes][4];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-#pragma unroll
-        for (int i = 0; i < kPlanes; ++i) words[i][g] = 0u;
+        unsigned long long b4[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int kk = kb + 4 * g + k;
-          const double v = (live && kk < kc) ? xr[(i64)kk * ldx] : 0.0;
-          put_digits((unsigned long long)__double_as_longlong(v), e, words, g, k);
+          b4[k] = (unsigned long long)__double_as_longlong((live && kk < kc) ? xr[(i64)kk * ldx] : 0.0);
         }
+        uint32_t w[kPlanes];
+        digits4(b4, e, w);
+#pragma unroll
+        for (int i = 0; i < kPlanes; ++i) words[i][g] = w[i];
       }
-      uint8_t* dst = planes + (i64)st * kPlanes * rows * kStage + plane_off(row, h);
+      uint8_t* dst = planes + ((i64)(row / kTcM) * nst + st) * kTcABytes + plane_off(row % kTcM, h);
 #pragma unroll
       for (int i = 0; i < kPlanes; ++i) {
         uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
-        *reinterpret_cast<uint4*>(dst + (i64)i * rows * kStage) = v;
+        *reinterpret_cast<uint4*>(dst + (i64)i * kTcM * kStage) = v;
       }
     }
   }
@@ -329,7 +360,7 @@ struct OzArgs {
   const int* ex;
   const int* ey;
   int p, q;           // extents (projection: p x q; update: rows of the chunk x N)
-  int cpx, cpy;       // padded column counts of the plane blocks
+  int tiles_p;        // tiles of X in the plane layout (projection: per sub-chunk)
   int nst;            // stages per tile (projection: kStagesPerSub)
   int tiles_q;
   int s_off;          // projection: sub-chunk index offset of this launch in the partial buffer
@@ -339,29 +370,26 @@ struct OzArgs {
   int* status;
 };
 
-// One 128 x 32 tile.  Projection (NN = false): grid (tiles_q, tiles_p, nsub),
-// the tile of sub-chunk s goes to the partial buffer.  Update (NN = true):
-// a linear grid with the q tile fastest (the blocks of one row tile run
-// together and share its X planes in L2), and C -= tile.
-template <bool NN>
+// Projections: one 128 x 32 tile of one sub-chunk per block, grid
+// (tiles_q, tiles_p, nsub) with the q tile fastest (the blocks running
+// together share the X planes of a sub-chunk in L2); the tile goes to the
+// sub-chunk's partial.
 __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
   extern __shared__ uint8_t tc_raw[];
   __shared__ __align__(8) uint64_t full_bar[kTcRing], empty_bar[kTcRing], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int give_up;
   if (a.status && *a.status) return;  // uniform across the block, before any allocation
-  int s, p0, q0;
-  if (NN) {
-    s = 0;
-    q0 = (int)(blockIdx.x % (unsigned)a.tiles_q) * kTcN;
-    p0 = (int)(blockIdx.x / (unsigned)a.tiles_q) * kTcM;
-  } else {
-    q0 = blockIdx.x * kTcN;
-    p0 = blockIdx.y * kTcM;
-    s = blockIdx.z;
-  }
+  const int q0 = blockIdx.x * kTcN, p0 = blockIdx.y * kTcM, s = blockIdx.z;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+  // scales of the epilogue, fetched first so that their latency hides behind the contraction
+  __shared__ int ey_s[kTcN];
+  const int r = 32 * warp + lane;  // tile row = TMEM lane
+  const int pr = p0 + r;
+  const bool live = pr < a.p;
+  const int exr = live ? a.ex[(i64)s * a.p + pr] : kExpZero;
+  if (t < kTcN) ey_s[t] = q0 + t < a.q ? a.ey[(i64)s * a.q + q0 + t] : kExpZero;
   if (t == 0) {
     for (int i = 0; i < kTcRing; ++i) {
       mbar_init(smem_u32(&full_bar[i]), 1);
@@ -387,9 +415,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
   __syncthreads();
   tc_fence_after();
   const int nst = a.nst;
-  const i64 stage_x = (i64)kPlanes * a.cpx * kStage, stage_y = (i64)kPlanes * a.cpy * kStage;
-  const uint8_t* gx = a.px + (i64)s * kStagesPerSub * stage_x + (i64)p0 * kStage;
-  const uint8_t* gy = a.py + (i64)s * kStagesPerSub * stage_y + (i64)q0 * kStage;
+  // this tile's stages: tile-major plane layout, kStagesPerSub stages per (sub-chunk, tile)
+  const uint8_t* gx = a.px + ((i64)s * a.tiles_p + p0 / kTcM) * kStagesPerSub * kTcABytes;
+  const uint8_t* gy = a.py + ((i64)s * a.tiles_q + q0 / kTcN) * kStagesPerSub * kTcBBytes;
 
   if (warp == 0 && lane == 0) {
     // producer: bulk copies of stage st into ring slot st % kTcRing
@@ -404,13 +432,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
       const uint32_t fb = smem_u32(&full_bar[slot]);
       const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
       mbar_expect_tx(fb, kTcStageBytes);
-      const uint8_t* xs = gx + st * stage_x;
-      const uint8_t* ys = gy + st * stage_y;
-#pragma unroll 1
-      for (int i = 0; i < kPlanes; ++i) {
-        bulk_g2s(sa + i * (kTcM * kStage), xs + (i64)i * a.cpx * kStage, kTcM * kStage, fb);
-        bulk_g2s(sb + i * (kTcN * kStage), ys + (i64)i * a.cpy * kStage, kTcN * kStage, fb);
-      }
+      bulk_g2s(sa, gx + (i64)st * kTcABytes, kTcABytes, fb);
+      bulk_g2s(sb, gy + (i64)st * kTcBBytes, kTcBBytes, fb);
       issued = st + 1;
     }
     // before leaving, every issued copy must have landed (bounded)
@@ -448,12 +471,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
     if (t == 0 && a.status) atomicCAS(a.status, 0, CQR_STATUS_TIMEOUT);
   } else {
     // epilogue: row r of the tile (TMEM lane r), 8 columns at a time
-    const int r = 32 * warp + lane;
-    const int pr = p0 + r;
-    const bool live = pr < a.p;
-    const int exr = live ? a.ex[(i64)s * a.p + pr] : kExpZero;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll 1
+#pragma unroll
     for (int c0 = 0; c0 < kTcN; c0 += 8) {
       long long g[2][8];
 #pragma unroll
@@ -475,7 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
       for (int j = 0; j < 8; ++j) {
         const int qc = q0 + c0 + j;
         if (!live || qc >= a.q) continue;
-        const int eyc = a.ey[(i64)s * a.q + qc];
+        const int eyc = ey_s[c0 + j];
         double v;
         if (exr == kExpBad || eyc == kExpBad) {
           v = __longlong_as_double(0x7ff8000000000000LL);
@@ -486,17 +505,209 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
           const int e2 = exr + eyc - 112 + 4 * kLevelLo;
           v = scaled_int(g[1][j], e2 + 28) + scaled_int(g[0][j], e2);  // one rounding
         }
-        if (NN) {
-          double* cp = a.C + pr + (i64)qc * a.ldc;
-          *cp -= v;
-        } else {
-          a.part[(i64)(a.s_off + s) * a.p * a.q + pr + (i64)qc * a.p] = v;
+        a.part[(i64)(a.s_off + s) * a.p * a.q + pr + (i64)qc * a.p] = v;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
+// ---------------------------------------------------------------------------
+// Updates C -= X Y as a persistent, warp-specialised kernel: block c takes
+// tiles c, c + G, c + 2G, ... (G = grid size; tile T is row tile T / tiles_q,
+// column tile T % tiles_q, so the blocks running together share row tiles).
+// Warp 0 streams the stages of all its tiles through a two-stage ring, warp 1
+// issues the MMAs of a tile into the one set of TMEM level regions, and warps
+// 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue in two phases: first
+// the level sums become the exact 64-bit group sums, parked in shared memory,
+// and the zeroed regions are handed back to warp 1 at once; then, while the
+// next tile's MMAs run, the group sums are scaled, added and subtracted from
+// C.  An update has only K / 32 stages per tile (4 for K = 128), so without
+// this overlap the fill and the epilogue would cost as much as the MMAs.
+constexpr int kUpRing = 2;
+constexpr int kUpThreads = 192;
+constexpr int kUpGroupBytes = 2 * kTcM * kTcN * (int)sizeof(long long);  // g0, g1 of one tile
+constexpr int kUpSmem = 1024 + kUpRing * kTcStageBytes + kUpGroupBytes;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a, int ntiles) {
+  extern __shared__ uint8_t up_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kUpRing], empty_bar[kUpRing], acc_full, acc_empty, mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int give_up;
+  if (a.status && *a.status) return;  // uniform across the block, before any allocation
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(up_raw) + 1023) & ~(uintptr_t)1023);
+  long long* g0s = reinterpret_cast<long long*>(ring + kUpRing * kTcStageBytes);  // [col][row]
+  long long* g1s = g0s + kTcM * kTcN;
+  if (t == 0) {
+    for (int i = 0; i < kUpRing; ++i) {
+      mbar_init(smem_u32(&full_bar[i]), 1);
+      mbar_init(smem_u32(&empty_bar[i]), 1);
+    }
+    mbar_init(smem_u32(&acc_full), 1);
+    mbar_init(smem_u32(&acc_empty), 4);  // one arrival per epilogue warp
+    mbar_init(smem_u32(&mma_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    give_up = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (warp >= 2) {  // the MMAs accumulate: zero the regions of this warp's lane quarter
+    for (int c = 0; c < (int)kTcCols; c += 32) tc_st_zero32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c);
+    tc_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const int nst = a.nst;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int g = 0;
+      bool stop = false;
+      for (int T = blockIdx.x; T < ntiles && !stop; T += gridDim.x) {
+        // tile-major planes: nst stages per X tile, kStagesPerSub per Y tile
+        const uint8_t* gx = a.px + (i64)(T / a.tiles_q) * nst * kTcABytes;
+        const uint8_t* gy = a.py + (i64)(T % a.tiles_q) * kStagesPerSub * kTcBBytes;
+        for (int st = 0; st < nst; ++st) {
+          const int slot = g % kUpRing;
+          if (g >= kUpRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((g / kUpRing - 1) & 1))) {
+            atomicExch(&give_up, 1);
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)&give_up) {
+            stop = true;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[slot]);
+          const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
+          mbar_expect_tx(fb, kTcStageBytes);
+          bulk_g2s(sa, gx + (i64)st * kTcABytes, kTcABytes, fb);
+          bulk_g2s(sb, gy + (i64)st * kTcBBytes, kTcBBytes, fb);
+          ++g;
+        }
+      }
+      // every issued copy must have landed before the block leaves (bounded)
+      for (int h = g - kUpRing < 0 ? 0 : g - kUpRing; h < g; ++h)
+        mbar_wait(smem_u32(&full_bar[h % kUpRing]), (uint32_t)((h / kUpRing) & 1));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int g = 0, k = 0;
+      bool stop = false;
+      for (int T = blockIdx.x; T < ntiles && !stop; T += gridDim.x, ++k) {
+        if (k >= 1 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((k - 1) & 1))) {
+          atomicExch(&give_up, 1);
+          break;
+        }
+        tc_fence_after();
+        for (int st = 0; st < nst; ++st) {
+          const int slot = g % kUpRing;
+          if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((g / kUpRing) & 1)) || *(volatile int*)&give_up) {
+            atomicExch(&give_up, 1);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
+          const uint64_t ad0 = tc_desc(sa), bd0 = tc_desc(sb);
+#pragma unroll
+          for (int u = 0; u < 22; ++u) {
+            const TcMma e = kTcSchedule[u];
+            const uint64_t ad = ad0 + (uint64_t)((e.i * kTcM * kStage) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((e.j0 * kTcN * kStage) >> 4);
+            tc_mma(tmem + (uint32_t)((e.i + e.j0 - kRegionLo) * kTcN), ad, bd, e.n);
+          }
+          tc_commit(smem_u32(&empty_bar[slot]));
+          ++g;
+        }
+        tc_commit(smem_u32(&acc_full));
+      }
+      tc_commit(smem_u32(&mma_done));  // every MMA issued above has completed when this arrives
+      mbar_wait(smem_u32(&mma_done), 0);
+    }
+  } else {
+    // epilogue: TMEM lane quarter qw, tile row r
+    const int qw = warp & 3, r = 32 * qw + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * qw) << 16);
+    int k = 0;
+    for (int T = blockIdx.x; T < ntiles; T += gridDim.x, ++k) {
+      const int p0 = (T / a.tiles_q) * kTcM, q0 = (T % a.tiles_q) * kTcN;
+      const bool ok = mbar_wait(smem_u32(&acc_full), (uint32_t)(k & 1));
+      if (!__all_sync(0xffffffffu, ok) || *(volatile int*)&give_up) {
+        atomicExch(&give_up, 1);
+        break;
+      }
+      tc_fence_after();
+      // phase 1: level sums -> exact group sums g0 (levels 13..19), g1 (20..26)
+#pragma unroll
+      for (int c0 = 0; c0 < kTcN; c0 += 8) {
+#pragma unroll
+        for (int grp = 1; grp >= 0; --grp) {
+          uint32_t v[7][8];
+#pragma unroll
+          for (int l = 6; l >= 0; --l)
+            tc_ld8(lane_base + (uint32_t)((kLevelLo - kRegionLo + 7 * grp + l) * kTcN + c0), v[l]);
+          tc_wait_ld();
+          long long* gs = grp ? g1s : g0s;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            long long acc = 0;
+#pragma unroll
+            for (int l = 6; l >= 0; --l) acc = acc * 16 + __float2int_rz(__uint_as_float(v[l][j]));
+            gs[(c0 + j) * kTcM + r] = acc;
+          }
+        }
+      }
+      // hand the zeroed regions back to the MMA warp
+      for (int c = 0; c < (int)kTcCols; c += 32) tc_st_zero32(lane_base + (uint32_t)c);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
+      // phase 2 (overlaps the next tile's MMAs): scale, add the two groups, subtract from C
+      const int pr = p0 + r;
+      if (pr < a.p) {
+        const int exr = a.ex[pr];
+        double cv[kTcN];
+#pragma unroll
+        for (int j = 0; j < kTcN; ++j) cv[j] = q0 + j < a.q ? a.C[pr + (i64)(q0 + j) * a.ldc] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kTcN; ++j) {
+          const int qc = q0 + j;
+          if (qc >= a.q) continue;
+          const int eyc = a.ey[qc];
+          double v;
+          if (exr == kExpBad || eyc == kExpBad) {
+            v = __longlong_as_double(0x7ff8000000000000LL);
+          } else if (exr == kExpZero || eyc == kExpZero) {
+            v = 0.0;
+          } else {
+            const int e2 = exr + eyc - 112 + 4 * kLevelLo;
+            v = scaled_int(g1s[j * kTcM + r], e2 + 28) + scaled_int(g0s[j * kTcM + r], e2);  // one rounding
+          }
+          a.C[pr + (i64)qc * a.ldc] = cv[j] - v;
         }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
+  if (t == 0 && give_up && a.status) atomicCAS(a.status, 0, CQR_STATUS_TIMEOUT);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
@@ -511,11 +722,18 @@ __global__ void ozaki_reduce_kernel(const double* part, i64 nsub, int p, int q, 
   C[r + (i64)c * ldc] = s;
 }
 
-template <bool NN>
+void up_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(ozaki_tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmem);
+    done = true;
+  }
+}
+
 void tc_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(ozaki_tc_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(ozaki_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     done = true;
   }
 }
@@ -569,7 +787,7 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
   off += sizeof(int) * (size_t)nsub_ch * (p + q);
   off = (off + 255) & ~(size_t)255;
   double* part = (double*)((char*)ws + off);
-  tc_attr<false>();
+  tc_attr();
   uint8_t* px = planes;
   uint8_t* py = planes + (size_t)nsub_ch * kPlanes * cpx * kSub;
   int* ex = exps;
@@ -578,10 +796,10 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
   for (i64 r0 = 0; r0 < m; r0 += ch) {
     const i64 nsub = ((m - r0 < ch ? m - r0 : ch) + kSub - 1) / kSub;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)p), 256, 0, st>>>(X, ldx, m, r0, p, cpx, px, ex, status);
+    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)p), 256, 0, st>>>(X, ldx, m, r0, p, kTcM, px, ex, status);
     prof_end(kMisc, 0.0, st);
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)q), 256, 0, st>>>(Y, ldy, m, r0, q, cpy, py, ey, status);
+    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)q), 256, 0, st>>>(Y, ldy, m, r0, q, kTcN, py, ey, status);
     prof_end(kMisc, 0.0, st);
     OzArgs a{};
     a.px = px;
@@ -590,15 +808,14 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
     a.ey = ey;
     a.p = p;
     a.q = q;
-    a.cpx = cpx;
-    a.cpy = cpy;
+    a.tiles_p = tiles_p;
     a.nst = kStagesPerSub;
     a.tiles_q = tiles_q;
     a.s_off = (int)(r0 / kSub);
     a.part = part;
     a.status = const_cast<int*>(status);
     prof_begin(kProjection, st);
-    ozaki_tc_kernel<false><<<dim3((unsigned)tiles_q, (unsigned)tiles_p, (unsigned)nsub), kTcThreads, kTcSmem, st>>>(a);
+    ozaki_tc_kernel<<<dim3((unsigned)tiles_q, (unsigned)tiles_p, (unsigned)nsub), kTcThreads, kTcSmem, st>>>(a);
     prof_end(kProjection, 2.0 * (double)(nsub * kSub < m - r0 ? nsub * kSub : m - r0) * p * q, st);
   }
   const i64 pq = (i64)p * q;
@@ -639,13 +856,13 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
   off = (off + (size_t)kSub * kPlanes * cpy + 255) & ~(size_t)255;
   int* ex = (int*)((char*)ws + off);
   int* ey = ex + rows;
-  tc_attr<true>();
+  up_attr();
   const int tiles_q = cpy / kTcN;
   for (i64 k0 = 0; k0 < K; k0 += kSub) {
     const int kc = (int)(K - k0 < kSub ? K - k0 : kSub);
     const int nst = (kc + kStage - 1) / kStage;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3(1u, (unsigned)N), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, cpy, py, ey, status);
+    ozaki_split_kernel<<<dim3(1u, (unsigned)N), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, kTcN, py, ey, status);
     prof_end(kMisc, 0.0, st);
     for (i64 r0 = 0; r0 < M; r0 += rows) {
       const i64 live = M - r0 < rows ? M - r0 : rows;
@@ -660,15 +877,15 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
       a.ey = ey;
       a.p = (int)live;
       a.q = N;
-      a.cpx = rws;
-      a.cpy = cpy;
+      a.tiles_p = rws / kTcM;
       a.nst = nst;
       a.tiles_q = tiles_q;
       a.C = C + r0;
       a.ldc = ldc;
       a.status = const_cast<int*>(status);
+      const int ntiles = (rws / kTcM) * tiles_q;
       prof_begin(kUpdate, st);
-      ozaki_tc_kernel<true><<<(unsigned)((i64)(rws / kTcM) * tiles_q), kTcThreads, kTcSmem, st>>>(a);
+      ozaki_tc_update_kernel<<<(unsigned)(ntiles < kSMs ? ntiles : kSMs), kUpThreads, kUpSmem, st>>>(a, ntiles);
       prof_end(kUpdate, 2.0 * (double)live * N * kc, st);
     }
   }
