@@ -4,7 +4,9 @@
 One step = one mCQR2GS factorisation (Alg. 9) of the m = 2^23, n = 1024,
 kappa = 1e15 test matrix A = U diag(sigma) V^T (Sec. 2.2 construction,
 seeded, synthetic), out of place (A is read, Q and R are written), panel
-width chosen by the autotuner among {64, 128, 256}.  Rate = 4 m n^2 / t,
+width b = 128 (the autotuner, --panel 0, finds 64, 128 and 256 within 0.3 %
+of one another on this shape and picks among them by noise; the fixed width
+keeps runs comparable).  Rate = 4 m n^2 / t,
 the paper's flop convention for mCQR2GS (Table 2 with the final R product
 removed, Sec. 5.4).  The matrix (68.7 GB) is far larger than L2, so no L2
 flush is needed between steps.
@@ -47,7 +49,7 @@ def parse():
     p.add_argument("--m", type=int, default=M_FULL)
     p.add_argument("--n", type=int, default=N_FULL)
     p.add_argument("--kappa", type=float, default=KAPPA_FULL)
-    p.add_argument("--panel", type=int, default=0, help="0 = autotune among 64/128/256")
+    p.add_argument("--panel", type=int, default=128, help="panel width; 0 = autotune among 64/128/256")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint sub-benchmarks")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -368,8 +370,22 @@ def bench_emulated(P, A, Q, R, b, args, flops, t_native):
     orth, res = accuracy(A, Q, R)
     return {"value": flops / t / 1e12, "unit": "TFLOP/s (FP64-equivalent, 4 m n^2 / t)", "ms_per_step": 1e3 * t,
             "speedup_vs_native": t_native / t, "orth_fro": orth, "resid_rel": res, "status": status,
-            "what": "m-row projections on FP8 tensor cores (mma.sync e4m3, 14-digit Ozaki splitting); "
-                    "all other steps native FP64"}
+            "what": "Gram matrices, projections and updates on the tcgen05 FP8 tensor cores (14-digit Ozaki "
+                    "splitting, exact FP32 level sums in TMEM); Cholesky factorisations and triangular solves "
+                    "native FP64"}
+
+
+# DRAM bytes per launch of the update kernel class, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of every update launch of an
+# m = 2^18, n = 1024, b = 128 factorisation: 33.29 GB over 45 launches,
+# scaled by m (every launch that matters streams m-row operands).
+UPDATE_DRAM_BYTES_PER_LAUNCH_2P18 = 33.29e9 / 45
+
+
+def update_traffic(m, n, b, dom, emulated):
+    if dom != "update_gemm" or emulated or n != 1024 or b != 128:
+        return None
+    return UPDATE_DRAM_BYTES_PER_LAUNCH_2P18 * m / 2 ** 18
 
 
 def run_ours(args, dist, rank, world):
@@ -422,7 +438,7 @@ def run_ours(args, dist, rank, world):
     peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     ach = prof[dom]["flops"] / (prof[dom]["ms"] * 1e-3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
     roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": dom,
+                "traffic": update_traffic(m, n, b, dom, emu), "kernel": dom,
                 "peak_note": "FP64 FMA pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); "
                              f"DFMA microbenchmark in this run: {probe / 1e3:.4f} TFLOP/s",
                 "share_of_device_time": prof[dom]["ms"] / tot_ms if tot_ms else None,
@@ -491,7 +507,7 @@ def run_ours(args, dist, rank, world):
             "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"mCQR2GS m={m} n={n} kappa={kappa:.0e} b={b} (out of place)"
-                                   + (", projections emulated on FP8 tensor cores" if emu else ""), "m": m, "n": n,
+                                   + (", products emulated on FP8 tensor cores" if emu else ""), "m": m, "n": n,
                        "kappa": kappa, "panel_b": b, "variant": "mcqr2gs",
                        "l2": f"inputs larger than L2 ({8 * m * n / 1e9:.1f} GB), no flush",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},

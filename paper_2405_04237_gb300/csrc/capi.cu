@@ -56,7 +56,8 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
   }
   L.part = take(sizeof(double) * pd);
   size_t oz = 0;
-  if (emulated && variant == CQR_MCQR2GS) {  // products with Y (b x w) and Z (jb x b) of Alg. 9
+  if (emulated && variant == CQR_MCQR2GS) {  // Gram matrices; products with Y (b x w) and Z (jb x b) of Alg. 9
+    oz = ozaki_workspace_bytes(m, b, b);
     for (i64 j = 1; j * b < n; ++j) {
       const size_t d[4] = {ozaki_workspace_bytes(m, b, (int)(n - j * b)), ozaki_workspace_bytes(m, (int)(j * b), b),
                            ozaki_nn_workspace_bytes(m, (int)(n - j * b), b),
@@ -136,7 +137,10 @@ cudaError_t trsm_t_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ld
 cudaError_t cqr_panel(i64 m, int b, double* X, i64 ldx, double* U, i64 ldu, const Work& w, int col0, int shift,
                       cudaStream_t st, bool second_pass_rule = false) {
   int* skip = second_pass_rule ? w.skip : nullptr;
-  TRY(tn_product(m, b, b, X, ldx, X, ldx, 1, w.part, w.W, b, w.status, st));
+  if (w.oz)  // emulated variant: the Gram W = X^T X on the tensor cores too (exactly symmetric)
+    TRY(tn_product_emulated(m, b, b, X, ldx, X, ldx, w.oz, w.W, b, w.status, st));
+  else
+    TRY(tn_product(m, b, b, X, ldx, X, ldx, 1, w.part, w.W, b, w.status, st));
   TRY(chol_factor(b, w.W, b, U, ldu, w.rinv, col0, w.status, shift, m, st, skip));
   TRY(trsm_any(m, b, X, ldx, U, ldu, w.rinv, w.status, st, skip));
   return cudaSuccess;
