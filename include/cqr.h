@@ -69,21 +69,22 @@ enum cqr_variant {
 #define CQR_ADAPTIVE 0x200
 
 /* Flag OR-ed into `variant` of cqr_factor and cqr_workspace_size (MCQR2GS
- * only): the m-row products of Alg. 9 -- the projections Y = Q_{j-1}^T
- * A_{j:k} and Z = Q_{1:j-1}^T P (steps 3 and 7) and the updates
- * A_{j:k} -= Q_{j-1} Y and P -= Q_{1:j-1} Z (steps 4 and 7) -- run on the FP8
- * tensor cores with an error-free splitting of the FP64 operands (Ozaki
- * scheme): each operand is scaled by powers of two along the contraction
- * (per column and 4096-row sub-chunk for a projection, per row for an
- * update) and cut into 14 signed 4-bit digits (56 bits); the 105 most
- * significant digit-plane pairs are multiplied exactly (FP32 accumulation of
- * integers < 2^24) and recombined in FP64.  Not FP64 arithmetic, but
- * FP64-accurate: the truncation drops terms below about 2^-52 of the scales'
- * product.  The Gram matrices, Cholesky factorisations and triangular solves
- * stay native FP64.  The update then runs unsplit on the caller's stream, so
- * CQR_LOOKAHEAD has no effect with this flag.  The workspace grows
- * (cqr_workspace_size with the flag) by the digit planes of one row chunk
- * (about 1 GiB) and one FP64 partial per 4096 rows. */
+ * only): every m-row product of Alg. 9 -- the Gram matrices W = X^T X
+ * (Alg. 1 step 1), the projections Y = Q_{j-1}^T A_{j:k} and
+ * Z = Q_{1:j-1}^T P (steps 3 and 7) and the updates A_{j:k} -= Q_{j-1} Y
+ * and P -= Q_{1:j-1} Z (steps 4 and 7) -- runs on the FP8 tensor cores
+ * (tcgen05, accumulators in TMEM) with an error-free splitting of the FP64
+ * operands (Ozaki scheme): each operand is scaled by powers of two along
+ * the contraction (per column and 4096-row sub-chunk for a Gram matrix or
+ * projection, per row for an update) and cut into 14 signed 4-bit digits
+ * (56 bits); the 105 most significant digit-plane pairs are multiplied
+ * exactly (FP32 accumulation of integers < 2^24) and recombined with one
+ * rounding.  Not FP64 arithmetic, but FP64-accurate: the truncation drops
+ * terms below about 2^-52 of the scales' product.  The Cholesky
+ * factorisations and triangular solves stay native FP64.  The update runs
+ * unsplit on the caller's stream, so CQR_LOOKAHEAD has no effect with this
+ * flag.  The workspace grows (cqr_workspace_size with the flag) by the digit
+ * planes of one row chunk (about 1 GiB) and one FP64 partial per 4096 rows. */
 #define CQR_EMULATED 0x400
 
 #define CQR_ERR_CUDA (-1000)

@@ -102,8 +102,8 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
     overlaps each trailing update with the next panel's CholeskyQR on a side
     stream (bitwise-identical results).  adaptive=True (mCQR2GS) applies the
     runtime choice of the second CholeskyQR pass per panel.  emulated=True
-    (mCQR2GS) runs the m-row projections and updates on the FP8 tensor cores
-    with the FP64-accurate Ozaki splitting.  check=True
+    (mCQR2GS) runs the m-row products (Gram matrices, projections, updates)
+    on the FP8 tensor cores with the FP64-accurate Ozaki splitting.  check=True
     synchronises the stream and raises CQRError on a Cholesky breakdown; with
     check=False the call is fully asynchronous (and graph-capturable when a
     workspace and outputs are supplied).

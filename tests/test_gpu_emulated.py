@@ -1,5 +1,6 @@
-"""Emulated projections (CQR_EMULATED): the m-row products Y = Q^T A and
-Z = Q^T P of Alg. 9 on the FP8 tensor cores with the error-free (Ozaki)
+"""Emulated products (CQR_EMULATED): the m-row products of Alg. 9 (Gram
+matrices, projections Y = Q^T A and Z = Q^T P, updates A -= Q Y and
+P -= Q Z) on the tcgen05 FP8 tensor cores with the error-free (Ozaki)
 splitting, checked against the FP64 oracle with the tolerances of the native
 path (orthogonality <= 1e-13, residual <= 1e-14, R <= 1e-11 for kappa <= 1e6)
 and bit for bit on exact dyadic inputs, where every digit product and every
@@ -70,3 +71,20 @@ def test_emulated_zero_and_nan_columns(cuda_lib, oracle):
     with pytest.raises(P.CQRError) as ei:
         gpu_factor(P, A, 8, emulated=True)
     assert ei.value.code > 0
+
+
+def test_emulated_contraction_beyond_one_chunk(cuda_lib):
+    """n > 4096 + b: the re-orthogonalisation update contracts over more than
+    4096 columns, so it runs in several contraction chunks (each with exact
+    level sums), and the Z projection spans 34 row tiles.  Checked against
+    the native FP64 factorisation on the GPU (kappa = 1e5, R within 1e-11)
+    and by the norms."""
+    P = cuda_lib
+    m, n, b = 8192, 4352, 64
+    A = P.colmajor(torch.from_numpy(make_test_matrix(m, n, 1e5, seed=5200)).cuda())
+    Qe, Re = P.factor(A, b, "mcqr2gs", emulated=True)
+    Qn, Rn = P.factor(A, b, "mcqr2gs")
+    eye = torch.eye(n, dtype=torch.float64, device="cuda")
+    assert torch.linalg.norm(eye - Qe.t() @ Qe).item() <= 1e-13 * (n / 1024)
+    assert (torch.linalg.norm(A - Qe @ Re) / torch.linalg.norm(A)).item() <= 1e-14
+    assert (torch.linalg.norm(Re - Rn) / torch.linalg.norm(Rn)).item() <= 1e-11
