@@ -300,32 +300,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-// D (TMEM) += A x B^T with N = 32 * nb (accumulating: the regions start zeroed)
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t ad, uint64_t bd, int nb) {
+// D (TMEM) = A x B^T (acc = 0) or D += A x B^T (acc = 1), N = 32 * nb
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t ad, uint64_t bd, int nb, uint32_t acc) {
   const uint32_t idesc = kTcIdescM | ((uint32_t)(kTcN * nb >> 3) << 17);
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(idesc));
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
-// zeros into 32 consecutive TMEM columns of this warp's 32 lanes
-__device__ __forceinline__ void tc_st_zero32(uint32_t taddr) {
-  const uint32_t z = 0;
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
-      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
-      "r"(z)
-      : "memory");
-}
-__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // The MMA schedule of one stage: (plane i of X, first plane j0 of Y, count n).
+// The first two write regions 2..9 and 10..15 (levels 13..26, every region
+// the epilogue reads) without overlap, so in the first stage of a tile they
+// run with acc = 0 and initialise the accumulators; regions 0 and 1 (levels
+// 11 and 12) only ever collect what is never read.
 struct TcMma {
   int i, j0, n;
 };
 __device__ constexpr TcMma kTcSchedule[22] = {
-    {11, 0, 8}, {12, 0, 8}, {13, 0, 8},                                  // i >= 11 with all of j = 0..7
-    {3, 8, 6},  {4, 8, 6},  {5, 8, 6},  {6, 8, 6},  {7, 8, 6}, {8, 8, 6},  // j = 8..13 for i >= 3
-    {9, 8, 6},  {10, 8, 6}, {11, 8, 6}, {12, 8, 6}, {13, 8, 6},
+    {13, 0, 8}, {13, 8, 6},                                              // i = 13: regions 2..9, 10..15
+    {11, 0, 8}, {12, 0, 8},                                              // i = 11, 12 with all of j = 0..7
+    {3, 8, 6},  {4, 8, 6},  {5, 8, 6},  {6, 8, 6},  {7, 8, 6}, {8, 8, 6},  // j = 8..13 for 3 <= i <= 12
+    {9, 8, 6},  {10, 8, 6}, {11, 8, 6}, {12, 8, 6},
     {6, 7, 1},  {7, 6, 2},  {8, 5, 3},  {9, 4, 4},  {10, 3, 5},            // j <= 7 with i + j >= 13, i <= 10
     {2, 11, 3}, {1, 12, 2}, {0, 13, 1}};                                 // j >= 11 with i + j >= 13, i <= 2
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -408,12 +403,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  // every MMA accumulates: zero the 16 level regions (each warp its 32 lanes)
-  for (int c = 0; c < (int)kTcCols; c += 32) tc_st_zero32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c);
-  tc_wait_st();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
   const int nst = a.nst;
   // this tile's stages: tile-major plane layout, kStagesPerSub stages per (sub-chunk, tile)
   const uint8_t* gx = a.px + ((i64)s * a.tiles_p + p0 / kTcM) * kStagesPerSub * kTcABytes;
@@ -456,7 +445,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
         const TcMma e = kTcSchedule[u];
         const uint64_t ad = ad0 + (uint64_t)((e.i * kTcM * kStage) >> 4);
         const uint64_t bd = bd0 + (uint64_t)((e.j0 * kTcN * kStage) >> 4);
-        tc_mma(tmem + (uint32_t)((e.i + e.j0 - kRegionLo) * kTcN), ad, bd, e.n);
+        tc_mma(tmem + (uint32_t)((e.i + e.j0 - kRegionLo) * kTcN), ad, bd, e.n, (st > 0 || u >= 2) ? 1u : 0u);
       }
       tc_commit(smem_u32(&empty_bar[slot]));
     }
@@ -522,7 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
 // issues the MMAs of a tile into the one set of TMEM level regions, and warps
 // 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue in two phases: first
 // the level sums become the exact 64-bit group sums, parked in shared memory,
-// and the zeroed regions are handed back to warp 1 at once; then, while the
+// and the regions are handed back to warp 1 at once; then, while the
 // next tile's MMAs run, the group sums are scaled, added and subtracted from
 // C.  An update has only K / 32 stages per tile (4 for K = 128), so without
 // this overlap the fill and the epilogue would cost as much as the MMAs.
@@ -565,13 +554,6 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  if (warp >= 2) {  // the MMAs accumulate: zero the regions of this warp's lane quarter
-    for (int c = 0; c < (int)kTcCols; c += 32) tc_st_zero32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c);
-    tc_wait_st();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
   const int nst = a.nst;
 
   if (warp == 0) {
@@ -630,7 +612,7 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
             const TcMma e = kTcSchedule[u];
             const uint64_t ad = ad0 + (uint64_t)((e.i * kTcM * kStage) >> 4);
             const uint64_t bd = bd0 + (uint64_t)((e.j0 * kTcN * kStage) >> 4);
-            tc_mma(tmem + (uint32_t)((e.i + e.j0 - kRegionLo) * kTcN), ad, bd, e.n);
+            tc_mma(tmem + (uint32_t)((e.i + e.j0 - kRegionLo) * kTcN), ad, bd, e.n, (st > 0 || u >= 2) ? 1u : 0u);
           }
           tc_commit(smem_u32(&empty_bar[slot]));
           ++g;
@@ -673,9 +655,7 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
           }
         }
       }
-      // hand the zeroed regions back to the MMA warp
-      for (int c = 0; c < (int)kTcCols; c += 32) tc_st_zero32(lane_base + (uint32_t)c);
-      tc_wait_st();
+      // hand the regions back to the MMA warp (the next tile's first stage overwrites them)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
