@@ -143,7 +143,9 @@ __device__ __forceinline__ i64 plane_off(i64 col, int half) {
 
 // ---------------------------------------------------------------------------
 // Column splitting: X (rows r0 .. r0 + nsub*kSub of an m x c matrix) ->
-// planes.  Grid (nsub, c); 256 threads; thread t handles rows 16t .. 16t+15
+// planes.  Grid (c, nsub), columns fastest: two neighbouring columns share
+// every 32-byte sector of the layout, so they are split together and the
+// sectors are completed while still in L2.  256 threads; thread t handles rows 16t .. 16t+15
 // of the sub-chunk (half t & 1 of stage t / 2).  Tiles of T columns; plane
 // block (s, tile, st, i) starts at byte
 // (((s * ntile + tile) * kStagesPerSub + st) * kPlanes + i) * T * 32 with
@@ -151,7 +153,7 @@ __device__ __forceinline__ i64 plane_off(i64 col, int half) {
 __global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c, int T,
                                                           uint8_t* planes, int* exps, const int* status) {
   if (status && *status) return;
-  const int s = blockIdx.x, col = blockIdx.y, t = threadIdx.x;
+  const int col = blockIdx.x, s = blockIdx.y, t = threadIdx.x;
   const i64 base = r0 + (i64)s * kSub + 16 * t;
   const double* xc = X + (i64)col * ldx;
   unsigned long long bits[16];
@@ -356,6 +358,7 @@ struct OzArgs {
   const int* ey;
   int p, q;           // extents (projection: p x q; update: rows of the chunk x N)
   int tiles_p;        // tiles of X in the plane layout (projection: per sub-chunk)
+  int y_in_x;         // projection X^T X: the Y tiles are read from the X planes (32-column slices)
   int nst;            // stages per tile (projection: kStagesPerSub)
   int tiles_q;
   int s_off;          // projection: sub-chunk index offset of this launch in the partial buffer
@@ -406,7 +409,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
   const int nst = a.nst;
   // this tile's stages: tile-major plane layout, kStagesPerSub stages per (sub-chunk, tile)
   const uint8_t* gx = a.px + ((i64)s * a.tiles_p + p0 / kTcM) * kStagesPerSub * kTcABytes;
-  const uint8_t* gy = a.py + ((i64)s * a.tiles_q + q0 / kTcN) * kStagesPerSub * kTcBBytes;
+  // Y tile: its own planes, or (X^T X) the 32-column slice q0 of the X tile holding it
+  const uint8_t* gy = a.y_in_x ? a.px + ((i64)s * a.tiles_p + q0 / kTcM) * kStagesPerSub * kTcABytes +
+                                     (i64)(q0 % kTcM) * kStage
+                               : a.py + ((i64)s * a.tiles_q + q0 / kTcN) * kStagesPerSub * kTcBBytes;
 
   if (warp == 0 && lane == 0) {
     // producer: bulk copies of stage st into ring slot st % kTcRing
@@ -422,7 +428,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
       const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
       mbar_expect_tx(fb, kTcStageBytes);
       bulk_g2s(sa, gx + (i64)st * kTcABytes, kTcABytes, fb);
-      bulk_g2s(sb, gy + (i64)st * kTcBBytes, kTcBBytes, fb);
+      if (a.y_in_x) {
+#pragma unroll 1
+        for (int i = 0; i < kPlanes; ++i)
+          bulk_g2s(sb + i * (kTcN * kStage), gy + (i64)st * kTcABytes + i * (kTcM * kStage), kTcN * kStage, fb);
+      } else {
+        bulk_g2s(sb, gy + (i64)st * kTcBBytes, kTcBBytes, fb);
+      }
       issued = st + 1;
     }
     // before leaving, every issued copy must have landed (bounded)
@@ -773,22 +785,26 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
   int* ex = exps;
   int* ey = exps + nsub_ch * p;
   const int tiles_p = cpx / kTcM, tiles_q = cpy / kTcN;
+  const bool same = X == Y && ldx == ldy && p == q;  // X^T X: split once
   for (i64 r0 = 0; r0 < m; r0 += ch) {
     const i64 nsub = ((m - r0 < ch ? m - r0 : ch) + kSub - 1) / kSub;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)p), 256, 0, st>>>(X, ldx, m, r0, p, kTcM, px, ex, status);
+    ozaki_split_kernel<<<dim3((unsigned)p, (unsigned)nsub), 256, 0, st>>>(X, ldx, m, r0, p, kTcM, px, ex, status);
     prof_end(kMisc, 0.0, st);
-    prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)nsub, (unsigned)q), 256, 0, st>>>(Y, ldy, m, r0, q, kTcN, py, ey, status);
-    prof_end(kMisc, 0.0, st);
+    if (!same) {
+      prof_begin(kMisc, st);
+      ozaki_split_kernel<<<dim3((unsigned)q, (unsigned)nsub), 256, 0, st>>>(Y, ldy, m, r0, q, kTcN, py, ey, status);
+      prof_end(kMisc, 0.0, st);
+    }
     OzArgs a{};
     a.px = px;
-    a.py = py;
+    a.py = same ? px : py;
     a.ex = ex;
-    a.ey = ey;
+    a.ey = same ? ex : ey;
     a.p = p;
     a.q = q;
     a.tiles_p = tiles_p;
+    a.y_in_x = same ? 1 : 0;
     a.nst = kStagesPerSub;
     a.tiles_q = tiles_q;
     a.s_off = (int)(r0 / kSub);
@@ -842,7 +858,7 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
     const int kc = (int)(K - k0 < kSub ? K - k0 : kSub);
     const int nst = (kc + kStage - 1) / kStage;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3(1u, (unsigned)N), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, kTcN, py, ey, status);
+    ozaki_split_kernel<<<dim3((unsigned)N, 1u), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, kTcN, py, ey, status);
     prof_end(kMisc, 0.0, st);
     for (i64 r0 = 0; r0 < M; r0 += rows) {
       const i64 live = M - r0 < rows ? M - r0 : rows;
