@@ -92,7 +92,9 @@ enum cqr_variant {
 #define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
 
 /* Largest panel width the library accepts (the one-CTA Cholesky keeps a
- * b x b Gram matrix in shared memory up to 128 and in L2 above). */
+ * b x b Gram matrix in shared memory up to 128 and in L2 above).  CQR_CQR2
+ * and CQR_SCQR3 factor the whole matrix as one panel (b = n), so they
+ * accept n <= CQR_MAX_PANEL only (argument error -2 beyond). */
 #define CQR_MAX_PANEL 512
 
 /*
@@ -113,7 +115,8 @@ int cqr_default_panel(int64_t n);
 
 /*
  * cqr_factor: A = Q R.
- *   m, n       rows and columns, m >= n >= 1                       (args 1, 2)
+ *   m, n       rows and columns, m >= n >= 1; n <= CQR_MAX_PANEL for
+ *              CQR_CQR2 and CQR_SCQR3                              (args 1, 2)
  *   A, lda     input, m x n, lda >= m.  Read-only unless Q == A    (args 3, 4)
  *   panel_b    panel width b; must divide n; 0 = cqr_default_panel(n).
  *              Ignored by CQR_CQR2 and CQR_SCQR3 (b = n)            (arg 5)

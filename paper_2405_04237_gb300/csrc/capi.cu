@@ -324,9 +324,9 @@ size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant_flags) 
   const bool emulated = (variant_flags & CQR_EMULATED) != 0;
   const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED);
   if (m < 1 || n < 1 || m < n || variant < 0 || variant > 3) return 0;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > CQR_MAX_PANEL) return 0;
   const int b = resolve_panel(n, panel_b, variant);
   if (b < 1 || b > CQR_MAX_PANEL || n % b) return 0;
-  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return 0;
   if (emulated && variant != CQR_MCQR2GS) return 0;
   return make_layout(m, n, b, variant, emulated).total;
 }
@@ -342,16 +342,16 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   if (!A) return -3;
   if (lda < m) return -4;
   if (variant < 0 || variant > 3) return -10;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > CQR_MAX_PANEL) return -2;  // one panel, b = n
   const int b = resolve_panel(n, panel_b, variant);
   if (panel_b < 0 || b < 1 || b > CQR_MAX_PANEL || n % b) return -5;
-  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return -2;
   if (!Q) return -6;
   if (ldq < m || (Q == A && ldq != lda)) return -7;
   if (Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
   if (!R) return -8;
   if (ldr < n) return -9;
   if (!workspace || ((uintptr_t)workspace & 255)) return -11;
-  if (emulated && variant != CQR_MCQR2GS) return -10;
+  if ((emulated || adaptive) && variant != CQR_MCQR2GS) return -10;
   const Layout L = make_layout(m, n, b, variant, emulated);
   if (ws_bytes < L.total) return -12;
   cudaStream_t st = (cudaStream_t)stream;
@@ -363,7 +363,6 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
                                   cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return CQR_ERR_CUDA;
   if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
-  if (adaptive && variant != CQR_MCQR2GS) return -10;
   if (lookahead && (variant == CQR_MCQR2GS || variant == CQR_CQR2GS)) {
     std::lock_guard<std::mutex> lk(g_side_mu);
     const Side* side = get_side();
@@ -628,9 +627,9 @@ int cqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int panel_b
   if (!A) return -3;
   if (lda < m) return -4;
   if (variant < 0 || variant > 3) return -10;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > CQR_MAX_PANEL) return -2;  // one panel, b = n
   const int b = resolve_panel(n, panel_b, variant);
   if (panel_b < 0 || b < 1 || b > CQR_MAX_PANEL || n % b) return -5;
-  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > 4096) return -2;
   if (!Q) return -6;
   if (ldq < m || (Q == A && ldq != lda)) return -7;
   if (Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
