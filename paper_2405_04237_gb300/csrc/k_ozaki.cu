@@ -519,18 +519,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
 // Updates C -= X Y as a persistent, warp-specialised kernel: block c takes
 // tiles c, c + G, c + 2G, ... (G = grid size; tile T is row tile T / tiles_q,
 // column tile T % tiles_q, so the blocks running together share row tiles).
-// Warp 0 streams the stages of all its tiles through a two-stage ring, warp 1
-// issues the MMAs of a tile into the one set of TMEM level regions, and warps
-// 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue in two phases: first
-// the level sums become the exact 64-bit group sums, parked in shared memory,
-// and the regions are handed back to warp 1 at once; then, while the
-// next tile's MMAs run, the group sums are scaled, added and subtracted from
-// C.  An update has only K / 32 stages per tile (4 for K = 128), so without
+// Warp 0 streams the stages of all its tiles through a three-stage ring, warp
+// 1 issues the MMAs of a tile into the one set of TMEM level regions, and
+// warps 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue in two phases:
+// first the level sums become the exact 64-bit group sums, kept in registers
+// (two per column of the thread's row), and the regions are handed back to
+// warp 1 at once; then, while the next tile's MMAs run, the group sums are
+// scaled, added and subtracted from C.  An update has only K / 32 stages per tile (4 for K = 128), so without
 // this overlap the fill and the epilogue would cost as much as the MMAs.
-constexpr int kUpRing = 2;
+constexpr int kUpRing = 3;
 constexpr int kUpThreads = 192;
-constexpr int kUpGroupBytes = 2 * kTcM * kTcN * (int)sizeof(long long);  // g0, g1 of one tile
-constexpr int kUpSmem = 1024 + kUpRing * kTcStageBytes + kUpGroupBytes;
+constexpr int kUpSmem = 1024 + kUpRing * kTcStageBytes;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -544,8 +543,6 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
   if (a.status && *a.status) return;  // uniform across the block, before any allocation
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(up_raw) + 1023) & ~(uintptr_t)1023);
-  long long* g0s = reinterpret_cast<long long*>(ring + kUpRing * kTcStageBytes);  // [col][row]
-  long long* g1s = g0s + kTcM * kTcN;
   if (t == 0) {
     for (int i = 0; i < kUpRing; ++i) {
       mbar_init(smem_u32(&full_bar[i]), 1);
@@ -647,7 +644,8 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
         break;
       }
       tc_fence_after();
-      // phase 1: level sums -> exact group sums g0 (levels 13..19), g1 (20..26)
+      // phase 1: level sums -> exact group sums g0 (levels 13..19), g1 (20..26), kept in registers
+      long long g0[kTcN], g1[kTcN];
 #pragma unroll
       for (int c0 = 0; c0 < kTcN; c0 += 8) {
 #pragma unroll
@@ -657,13 +655,13 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
           for (int l = 6; l >= 0; --l)
             tc_ld8(lane_base + (uint32_t)((kLevelLo - kRegionLo + 7 * grp + l) * kTcN + c0), v[l]);
           tc_wait_ld();
-          long long* gs = grp ? g1s : g0s;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             long long acc = 0;
 #pragma unroll
             for (int l = 6; l >= 0; --l) acc = acc * 16 + __float2int_rz(__uint_as_float(v[l][j]));
-            gs[(c0 + j) * kTcM + r] = acc;
+            if (grp) g1[c0 + j] = acc;
+            else g0[c0 + j] = acc;
           }
         }
       }
@@ -671,28 +669,32 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty));
-      // phase 2 (overlaps the next tile's MMAs): scale, add the two groups, subtract from C
+      // phase 2 (overlaps the next tile's MMAs): scale, add the two groups, subtract from C,
+      // 16 columns at a time
       const int pr = p0 + r;
       if (pr < a.p) {
         const int exr = a.ex[pr];
-        double cv[kTcN];
 #pragma unroll
-        for (int j = 0; j < kTcN; ++j) cv[j] = q0 + j < a.q ? a.C[pr + (i64)(q0 + j) * a.ldc] : 0.0;
+        for (int h = 0; h < kTcN; h += 16) {
+          double cv[16];
 #pragma unroll
-        for (int j = 0; j < kTcN; ++j) {
-          const int qc = q0 + j;
-          if (qc >= a.q) continue;
-          const int eyc = a.ey[qc];
-          double v;
-          if (exr == kExpBad || eyc == kExpBad) {
-            v = __longlong_as_double(0x7ff8000000000000LL);
-          } else if (exr == kExpZero || eyc == kExpZero) {
-            v = 0.0;
-          } else {
-            const int e2 = exr + eyc - 112 + 4 * kLevelLo;
-            v = scaled_int(g1s[j * kTcM + r], e2 + 28) + scaled_int(g0s[j * kTcM + r], e2);  // one rounding
+          for (int j = 0; j < 16; ++j) cv[j] = q0 + h + j < a.q ? a.C[pr + (i64)(q0 + h + j) * a.ldc] : 0.0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int qc = q0 + h + j;
+            if (qc >= a.q) continue;
+            const int eyc = a.ey[qc];
+            double v;
+            if (exr == kExpBad || eyc == kExpBad) {
+              v = __longlong_as_double(0x7ff8000000000000LL);
+            } else if (exr == kExpZero || eyc == kExpZero) {
+              v = 0.0;
+            } else {
+              const int e2 = exr + eyc - 112 + 4 * kLevelLo;
+              v = scaled_int(g1[h + j], e2 + 28) + scaled_int(g0[h + j], e2);  // one rounding
+            }
+            a.C[pr + (i64)qc * a.ldc] = cv[j] - v;
           }
-          a.C[pr + (i64)qc * a.ldc] = cv[j] - v;
         }
       }
     }
