@@ -46,8 +46,9 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--m", type=int, default=M_FULL)
-    p.add_argument("--n", type=int, default=N_FULL)
+    # --rows / --cols: the same, for launchers (torch.distributed.run) that read --m / --n as their own prefixes
+    p.add_argument("--m", "--rows", dest="m", type=int, default=M_FULL)
+    p.add_argument("--n", "--cols", dest="n", type=int, default=N_FULL)
     p.add_argument("--kappa", type=float, default=KAPPA_FULL)
     p.add_argument("--panel", type=int, default=128, help="panel width; 0 = autotune among 64/128/256")
     p.add_argument("--no-e2e", action="store_true")
@@ -74,22 +75,29 @@ def dist_init(args):
     return None, 0, 1
 
 
+def _reduce_device(dist):
+    # NCCL reduces device tensors; gloo (the reference arm, CPU tests) host tensors
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def allreduce_max(dist, x):
+    """Maximum of x over the ranks (timing only: not on the data path)."""
     if dist is None:
         return x
     import torch
 
-    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def allreduce_sum(dist, x):
+    """Sum of x over the ranks (launch counts only)."""
     if dist is None:
         return x
     import torch
 
-    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
@@ -193,6 +201,15 @@ def cpu_baseline(n, b, kappa, target_s=20.0):
     return v, desc, oracle.num_threads(), dt, A.shape[0]
 
 
+def workload_config(m, n, kappa, b, emu, world):
+    """The "config" object of the JSON line (the same for both arms)."""
+    return {"workload": f"mCQR2GS m={m} n={n} kappa={kappa:.0e} b={b} (out of place)"
+                        + (", products emulated on FP8 tensor cores" if emu else ""), "m": m, "n": n,
+            "kappa": kappa, "panel_b": b, "variant": "mcqr2gs",
+            "l2": f"inputs larger than L2 ({8 * m * n / 1e9:.1f} GB), no flush",
+            "parallelism": "replicas" if world > 1 else "single-gpu"}
+
+
 def run_reference(args, dist, rank, world):
     if rank != 0:
         return
@@ -223,8 +240,7 @@ def run_reference(args, dist, rank, world):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"mCQR2GS m={args.m} n={args.n} kappa={args.kappa:.0e}", "m": args.m, "n": args.n,
-                   "kappa": args.kappa, "panel_b": b, "sample_rows": m_s},
+        "config": {**workload_config(args.m, args.n, args.kappa, b, False, world), "sample_rows": m_s},
         "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -507,11 +523,7 @@ def run_ours(args, dist, rank, world):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"mCQR2GS m={m} n={n} kappa={kappa:.0e} b={b} (out of place)"
-                                   + (", products emulated on FP8 tensor cores" if emu else ""), "m": m, "n": n,
-                       "kappa": kappa, "panel_b": b, "variant": "mcqr2gs",
-                       "l2": f"inputs larger than L2 ({8 * m * n / 1e9:.1f} GB), no flush",
-                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "config": workload_config(m, n, kappa, b, emu, world),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
