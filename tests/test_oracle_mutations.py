@@ -5,7 +5,9 @@ transposed operand, a factor product in the wrong order -- are planted in
 copies of oracle/cqr_oracle.c, each copy is compiled on its own, and the pin
 checks (the same facts test_oracle_pins.py uses: the exact dyadic QR,
 Householder by brute force, the paper's accuracy targets, the breakdown
-status, torch autograd for the adjoint) must reject every mutant.  The
+status, the closed form of the shifted CholeskyQR on orthonormal columns,
+the runtime repetition rule on both sides of its threshold, torch autograd
+for the adjoint) must reject every mutant.  The
 unmutated source must pass them all.
 """
 import os
@@ -15,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _helpers import load_exact_golden, orth_err, rel_diff, resid, sign_normalised_qr
+from _helpers import exact_qr_case, load_exact_golden, orth_err, rel_diff, resid, sign_normalised_qr
 from testmatrices import make_test_matrix
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "cqr_oracle.c")
@@ -51,6 +53,14 @@ MUTATIONS = [
     ("backward: R instead of R^T in the final solve", "        double u = AT(R, ldr, c, i);\n        for (i64 r = r0; r < r1; ++r) s[r - r0] -= ai[r] * u;",
      "        double u = AT(R, ldr, i, c);\n        for (i64 r = r0; r < r1; ++r) s[r - r0] -= ai[r] * u;"),
     ("householder: no sign normalisation", "    if (AT(R, ldr, j, j) < 0.0) {", "    if (0) {"),
+    ("scqr: shift subtracted", "for (i64 j = 0; j < b; ++j) W[j + j * b] += s;",
+     "for (i64 j = 0; j < b; ++j) W[j + j * b] -= s;"),
+    ("scqr: shift without sqrt(m)", "double s = sqrt((double)m) * ldexp(1.0, -53) * fro2;",
+     "double s = ldexp(1.0, -53) * fro2;"),
+    ("scqr3: one CholeskyQR after the shifted pass", "  if (!st) st = or_cqr2(m, n, X, ldx, R2, n);",
+     "  if (!st) st = or_cqr(m, n, X, ldx, R2, n);"),
+    ("adaptive: threshold too loose", "const double tau = 8.0 * ldexp(1.0, -53);", "const double tau = ldexp(1.0, -20);"),
+    ("adaptive: never fires", "const double tau = 8.0 * ldexp(1.0, -53);", "const double tau = 0.0;"),
 ]
 
 
@@ -105,6 +115,31 @@ def _pins(o) -> dict:
         return st == 3
 
     check("breakdown", breakdown)
+
+    def shifted():
+        # Alg. 4 on exactly orthonormal columns: W = I, s = sqrt(m) u n, R = sqrt(1 + s) I, Q = A / sqrt(1 + s)
+        _, Qo, _ = exact_qr_case(4096, 16, seed=11)
+        d = np.sqrt(1.0 + np.sqrt(4096.0) * 2.0 ** -53 * 16)
+        Q1, R1 = o.scqr(Qo)
+        ok = np.array_equal(R1, d * np.eye(16)) and np.array_equal(Q1, Qo / d)
+        X = make_test_matrix(2000, 30, 1e12, seed=9)
+        Q, R = o.scqr3(X)
+        return ok and orth_err(Q) < 1e-13 and resid(X, Q, R) < 1e-14 and np.all(np.diag(R) > 0)
+
+    check("shifted", shifted)
+
+    def adaptive():
+        # silent where the second pass matters (kappa = 1e4), fires on orthonormal panels (kappa = 1)
+        X = make_test_matrix(3000, 48, 1e4, seed=12)
+        Qd, Rd = o.mcqr2gs(X, 16)
+        Qa, Ra = o.mcqr2gs(X, 16, adaptive=True)
+        ok = np.array_equal(Qd, Qa) and np.array_equal(Rd, Ra)
+        X = make_test_matrix(3000, 48, 1.0, seed=13)
+        Qd, Rd = o.mcqr2gs(X, 16)
+        Qa, Ra = o.mcqr2gs(X, 16, adaptive=True)
+        return ok and not np.array_equal(Qd, Qa) and orth_err(Qa) < 1e-14 and resid(X, Qa, Ra) < 1e-15
+
+    check("adaptive", adaptive)
 
     def adjoint():
         import torch

@@ -245,6 +245,22 @@ def test_scqr3_survives_1e15(oracle):
     assert orth_err(Q) < 1e-13 and resid(A, Q, R) < 1e-14
 
 
+def test_scqr_shift_closed_form(oracle):
+    """Alg. 4 on exactly orthonormal columns (scaled Hadamard, every Gram sum
+    exact): W = I, the shift is s = sqrt(m) u ||A||_F^2 = sqrt(m) u n, so the
+    shifted Cholesky factor is sqrt(1 + s) I and Q = A / sqrt(1 + s), bit for
+    bit.  A wrong sign of the shift, a missing sqrt(m) or a shift off the
+    diagonal each changes the result."""
+    for m, n in [(4096, 16), (1024, 12), (256, 3)]:
+        _, Q0, _ = exact_qr_case(m, n, seed=m + n)
+        s = np.sqrt(float(m)) * U * n
+        assert s > 0 and (1.0 + s) != 1.0
+        d = np.sqrt(1.0 + s)
+        Q1, R1 = oracle.scqr(Q0)
+        assert np.array_equal(R1, d * np.eye(n)), (m, n)
+        assert np.array_equal(Q1, Q0 / d), (m, n)
+
+
 def test_literal_r_reading_is_rounding_level(oracle):
     """Alg. 9 leaves R of steps 6-8 implicit.  Adding the re-orthogonalisation
     coefficients (R_{1:j-1,j} += Z S1) is exact in exact arithmetic; dropping
