@@ -21,7 +21,9 @@
 // (8-column groups of 256 bytes, each two 8 x 16-byte core matrices holding
 // indices 0..15, then 16..31).  The 14 planes of one stage of one tile are
 // thus one contiguous run (56 KiB for X, 14 KiB for Y), and a stage arrives
-// in shared memory with two bulk asynchronous copies.
+// in shared memory with two bulk asynchronous copies (for a Gram matrix
+// X^T X, whose Y tiles are 32-column slices of the X planes, one copy for X
+// and one per plane for Y).
 //
 // Products.  x_a y_b = 2^(e_a + e_b - 112) sum_{i,j} d^x_i d^y_j 16^(i+j).
 // The 105 plane pairs with i + j >= 13 (the 14 most significant weight
