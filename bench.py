@@ -159,20 +159,26 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- CPU baseline (oracle)
-def oracle_sample(n, b, kappa, target_s):
+def oracle_sample(n, b, kappa, target_s, cap_rows=1 << 18):
     """A row sample of the workload (same n, b, kappa construction) sized so
-    that one oracle mCQR2GS on it takes about target_s seconds."""
+    that one oracle mCQR2GS on it takes about target_s seconds (between
+    target_s / 2 and target_s when the row cap allows).
+
+    The oracle runs its row sums in parallel over fixed 4096-row blocks, so
+    its time grows linearly with the rows only once every thread has a
+    block: the probe uses 4096 rows per thread, is run once untimed (thread
+    start-up, page faults), and is scaled up by doublings from there."""
     import oracle
     from testmatrices import make_test_matrix
 
     oracle.build()
-    m_s = 1 << 12
+    m_s = min(cap_rows, (1 << 12) * max(1, oracle.num_threads()))
     A = make_test_matrix(m_s, n, kappa, seed=SEED_FULL)
-    oracle.mcqr2gs(A, b, check=False)  # untimed: the first call pays for thread start-up and page faults
+    oracle.mcqr2gs(A, b, check=False)
     t0 = time.perf_counter()
     oracle.mcqr2gs(A, b, check=False)
     dt = time.perf_counter() - t0
-    while dt * 2 <= target_s and m_s < (1 << 18):
+    while dt * 2 <= target_s and m_s * 2 <= cap_rows:
         m_s *= 2
         dt *= 2
     if A.shape[0] != m_s:
