@@ -247,8 +247,9 @@ double cqr_probe_fp64_peak(int iters);
  * Launch accounting and kernel timing (measurement support; not in the
  * paper).  Kernel classes: 0 Gram (syrk partials), 1 projection (split-m
  * X^T Z partials), 2 split-m reduction, 3 Cholesky, 4 triangular solve,
- * 5 GEMM update (A -= Q Y, P -= Q Z, R products), 6 adjoint helpers and
- * probes, 7 batched scheduler.
+ * 5 GEMM update (A -= Q Y, P -= Q Z, R products), 6 other kernels (adjoint
+ * helpers, probes, the digit splitting of CQR_EMULATED), 7 batched
+ * scheduler.
  *
  * cqr_launch_count: number of kernels this process has launched through the
  *   library so far (host counter; monotonic).

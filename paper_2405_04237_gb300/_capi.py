@@ -31,7 +31,7 @@ EXPORTS = [
     "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak",
     "cqr_factor_noalloc", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
 ]
-KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "adjoint_misc",
+KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "misc",
                   "batched"]
 
 

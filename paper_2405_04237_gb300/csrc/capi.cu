@@ -475,6 +475,10 @@ struct StreamPool {
   bool ok = false;
 };
 StreamPool g_pool[64];  // per device
+// One batched call at a time enqueues on the pool: the fork event and the
+// streams are shared, so two host threads interleaving their records would
+// make one batch wait on the other's fork point.
+std::mutex g_pool_mu;
 
 StreamPool* get_pool() {
   int dev = 0;
@@ -532,6 +536,7 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
     if (!A[i] || !Q[i] || !R[i]) return -6;
     if (Q[i] != A[i] && overlaps(A[i], lda[i], m[i], n[i], Q[i], lda[i])) return -7;
   }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
   StreamPool* pool = get_pool();
   if (!pool) return CQR_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;

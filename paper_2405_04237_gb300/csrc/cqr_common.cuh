@@ -119,7 +119,7 @@ enum KernelClass {
   kCholesky = 3,
   kTrsm = 4,
   kUpdate = 5,     // C = beta C + alpha A B (GS / re-orthogonalisation updates, R products)
-  kMisc = 6,
+  kMisc = 6,       // adjoint helpers, probes, digit splitting of the emulated products
   kBatched = 7,
   kNumClasses = 8
 };

@@ -33,7 +33,7 @@ size_t g_cap = 0;
 thread_local int t_open = -1;
 
 const char* kNames[kNumClasses] = {"gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm",
-                                   "adjoint_misc", "batched"};
+                                   "misc", "batched"};
 
 }  // namespace
 
