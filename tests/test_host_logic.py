@@ -195,3 +195,9 @@ def test_autotuner_stability_filter():
     # narrow matrices: below the lower bound only b = n, else the widest stable divisor
     assert candidates(12, "mcqr2gs", 1e15) == [4]
     assert candidates(16, "mcqr2gs", 1e3) == [16]
+
+
+def test_kernel_class_names_match_the_binding(L):
+    names = [L.cqr_kernel_class_name(i).decode() for i in range(len(_capi.KERNEL_CLASSES))]
+    assert names == _capi.KERNEL_CLASSES
+    assert L.cqr_launch_count() >= 0
