@@ -13,7 +13,8 @@ works on column-major (Fortran-order) copies, so callers can pass any layout.
 Parity pins (what fixes each routine independently of itself) live in
 ``tests/test_oracle_pins.py``: the exact QR of dyadic inputs (closed form),
 Householder QR by brute force on tiny inputs, closed forms (R_11 = ||a_1||,
-orthogonal columns give a diagonal R), the b = n reductions, the paper's
+orthogonal columns give a diagonal R, the shifted CholeskyQR of exactly
+orthonormal columns gives sqrt(1 + s) I), the b = n reductions, the paper's
 stability claims (Sec. 4, Sec. 5.3-5.4) on scaled-down matrices, and finite
 differences / torch autograd for the adjoint.  ``tests/test_oracle_mutations.py``
 checks that those pins reject mutated copies of the C source.
