@@ -320,13 +320,43 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t ad, uint64_t bd, int
 struct TcMma {
   int i, j0, n;
 };
-__device__ constexpr TcMma kTcSchedule[22] = {
-    {13, 0, 8}, {13, 8, 6},                                              // i = 13: regions 2..9, 10..15
-    {11, 0, 8}, {12, 0, 8},                                              // i = 11, 12 with all of j = 0..7
-    {3, 8, 6},  {4, 8, 6},  {5, 8, 6},  {6, 8, 6},  {7, 8, 6}, {8, 8, 6},  // j = 8..13 for 3 <= i <= 12
-    {9, 8, 6},  {10, 8, 6}, {11, 8, 6}, {12, 8, 6},
-    {6, 7, 1},  {7, 6, 2},  {8, 5, 3},  {9, 4, 4},  {10, 3, 5},            // j <= 7 with i + j >= 13, i <= 10
-    {2, 11, 3}, {1, 12, 2}, {0, 13, 1}};                                 // j >= 11 with i + j >= 13, i <= 2
+#define CQR_TC_SCHEDULE                                                                         \
+  {13, 0, 8}, {13, 8, 6},                                              /* i = 13: regions 2..9, 10..15 */ \
+      {11, 0, 8}, {12, 0, 8},                                          /* i = 11, 12 with all of j = 0..7 */ \
+      {3, 8, 6}, {4, 8, 6}, {5, 8, 6}, {6, 8, 6}, {7, 8, 6}, {8, 8, 6}, /* j = 8..13 for 3 <= i <= 12 */ \
+      {9, 8, 6}, {10, 8, 6}, {11, 8, 6}, {12, 8, 6},                                                    \
+      {6, 7, 1}, {7, 6, 2}, {8, 5, 3}, {9, 4, 4}, {10, 3, 5}, /* j <= 7 with i + j >= 13, i <= 10 */     \
+      {2, 11, 3}, {1, 12, 2}, {0, 13, 1}                      /* j >= 11 with i + j >= 13, i <= 2 */
+__device__ constexpr TcMma kTcSchedule[22] = {CQR_TC_SCHEDULE};
+
+// Compile-time check of the same entries: every digit pair (i, j) of a kept
+// level (i + j >= 13) exactly once, no pair twice, every instruction within
+// the planes, N = 32 n <= 256, every region in TMEM, and the first two
+// instructions writing each read region (levels 13..26) exactly once and
+// nothing else (they run with the accumulate flag off).
+constexpr TcMma kTcScheduleCheck[22] = {CQR_TC_SCHEDULE};
+constexpr bool tc_schedule_ok() {
+  int count[kPlanes][kPlanes] = {};
+  int first[kTcCols / kTcN] = {};
+  for (int u = 0; u < 22; ++u) {
+    const TcMma e = kTcScheduleCheck[u];
+    if (e.i < 0 || e.i >= kPlanes || e.j0 < 0 || e.n < 1 || e.j0 + e.n > kPlanes || kTcN * e.n > 256) return false;
+    for (int v = 0; v < e.n; ++v) {
+      const int j = e.j0 + v, region = e.i + j - kRegionLo;
+      if (region < 0 || region >= (int)(kTcCols / kTcN)) return false;
+      ++count[e.i][j];
+      if (u < 2) ++first[region];
+    }
+  }
+  for (int i = 0; i < kPlanes; ++i)
+    for (int j = 0; j < kPlanes; ++j)
+      if (count[i][j] > 1 || (i + j >= kLevelLo && count[i][j] != 1)) return false;
+  for (int r = 0; r < (int)(kTcCols / kTcN); ++r)
+    if (first[r] != (r >= kLevelLo - kRegionLo ? 1 : 0)) return false;
+  return true;
+}
+static_assert(tc_schedule_ok(), "MMA schedule: kept pairs once, regions in range, first two initialise the read regions");
+#undef CQR_TC_SCHEDULE
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
