@@ -78,6 +78,9 @@ constexpr int kTcBBytes = kPlanes * kTcN * kStage;    // 14336
 constexpr int kTcStageBytes = kTcABytes + kTcBBytes;  // 71680
 constexpr int kTcSmem = kTcRing * kTcStageBytes + 1024;  // + alignment slack
 constexpr uint32_t kTcCols = 512;   // TMEM columns: 16 regions of kTcN, levels 11..26
+constexpr int kMaxDynSmem = 227 * 1024 - 1024;  // opt-in dynamic shared memory per block, less static use
+static_assert(kTcSmem <= kMaxDynSmem, "projection ring fits in shared memory");
+static_assert(kTcCols >= 32 && kTcCols <= 512 && (kTcCols & (kTcCols - 1)) == 0, "TMEM allocation: power of 2, 32..512");
 constexpr int kRegionLo = 11;       // level of TMEM region 0
 static_assert((2 * kPlanes - 1 - kRegionLo) * kTcN == (int)kTcCols, "level regions fill the TMEM allocation");
 static_assert(kLevelLo == 13 && kLevels == 14, "the MMA schedule and the two groups of seven levels");
@@ -562,6 +565,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
 constexpr int kUpRing = 3;
 constexpr int kUpThreads = 192;
 constexpr int kUpSmem = 1024 + kUpRing * kTcStageBytes;
+static_assert(kUpSmem <= kMaxDynSmem, "update ring fits in shared memory");
+static_assert(kUpThreads == 6 * 32, "producer, MMA issuer and one epilogue warp per TMEM lane quarter");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
