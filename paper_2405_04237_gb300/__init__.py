@@ -25,7 +25,7 @@ from ._capi import CQRError, VARIANTS, load, status_string
 __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
     "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "colmajor", "empty_colmajor",
-    "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size",
+    "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size", "qr_batched", "CQRBatchedFunction",
 ]
 
 
@@ -232,6 +232,39 @@ def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, s
         if bad:
             raise CQRError(int(status[bad[0]].item()), f"cqr_factor_batched (matrix {bad[0]})")
     return list(zip(Qs, Rs))
+
+
+class CQRBatchedFunction(torch.autograd.Function):
+    """Differentiable A_i -> (Q_i, R_i) for a list of matrices: one batched
+    forward call (cqr_factor_batched), one adjoint call (cqr_backward) per
+    matrix in the backward pass.  Saves only the outputs.  Each Q_i, R_i and
+    each gradient is bitwise the one of a single qr(A_i, b_i) call."""
+
+    @staticmethod
+    def forward(ctx, panel_b, variant, *As):
+        outs = factor_batched([A.detach() for A in As], panel_b, variant)
+        Qs = [Q for Q, _ in outs]
+        Rs = [R for _, R in outs]
+        ctx.save_for_backward(*Qs, *Rs)
+        ctx.count = len(As)
+        return (*Qs, *Rs)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        B = ctx.count
+        saved = ctx.saved_tensors
+        dAs = [backward(saved[i], saved[B + i], grads[i], grads[B + i]) for i in range(B)]
+        return (None, None, *dAs)
+
+
+def qr_batched(As, panel_b=None, variant="mcqr2gs"):
+    """Differentiable batched QR (see CQRBatchedFunction); returns a list of
+    (Q_i, R_i).  panel_b: one width for all, a list, or None (library default)."""
+    if len(As) == 0:
+        return []
+    out = CQRBatchedFunction.apply(panel_b, variant, *As)
+    B = len(As)
+    return list(zip(out[:B], out[B:]))
 
 
 class BatchedGraph:
