@@ -39,6 +39,9 @@ struct NnShape {
   static constexpr int NTM = TM / 4;
   static constexpr int KC = TM >= 256 ? 8 : 16;
   static constexpr int SA = TM + 2, SB = TN + 2;
+  static_assert(TM % 4 == 0 && TN % 4 == 0, "4 x 4 micro-tiles");
+  static_assert(NTM * (TN / 4) == kNnThreads, "one micro-tile per thread covers the TM x TN tile");
+  static_assert(KC * (SA + SB) * (int)sizeof(double) <= 48 * 1024, "static shared memory limit");
 };
 
 template <int TM, int TN, bool NEG>

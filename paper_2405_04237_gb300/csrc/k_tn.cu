@@ -181,6 +181,10 @@ struct TnShape {
   static constexpr int TILE_D = RB * (SP + SQ);
   static constexpr int RED_D = 16 * kTnThreads;
   static constexpr int SMEM_D = TILE_D > RED_D ? TILE_D : RED_D;
+  static_assert(TP % 4 == 0 && TQ % 4 == 0, "4 x 4 micro-tiles");
+  static_assert(NTG * G == kTnThreads, "every thread owns one micro-tile of one row group");
+  static_assert(RB >= G, "every row group gets rows");
+  static_assert(SMEM_D * (int)sizeof(double) <= 48 * 1024, "static shared memory limit");
 };
 
 template <int TP, int TQ>
