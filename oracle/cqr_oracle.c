@@ -35,6 +35,13 @@
  *                  mode rule M = R Rbar^T - Qbar^T Q,
  *                  Abar = (Qbar + Q copyltu(M)) R^{-T})
  *   or_householder textbook Householder QR, used only to pin the others
+ *
+ * Pins (tests/test_oracle_pins.py, tests/test_oracle_mutations.py): every
+ * function above is fixed by something other than itself -- exact dyadic
+ * QR, Householder/LAPACK by brute force, closed forms (including sCQR on
+ * orthonormal columns), the paper's reductions and stability claims, finite
+ * differences and torch autograd for the adjoint.  No function is parity
+ * unpinned.
  */
 #include <math.h>
 #include <stdint.h>
