@@ -60,7 +60,7 @@ def sign_normalised_r(A):
 
 def rows_match_solve(A, Q, R, kappa, count=4096, seed=7):
     """max |Q_s - A_s R^{-1}| over sampled rows, and its bound 100 kappa u max|Q_s|."""
-    from scipy.linalg import solve_triangular
+    solve_triangular = pytest.importorskip("scipy.linalg").solve_triangular
 
     rng = np.random.default_rng(seed)
     rows = torch.from_numpy(np.sort(rng.choice(A.shape[0], count, replace=False))).to(A.device)
