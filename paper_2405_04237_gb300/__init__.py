@@ -65,9 +65,11 @@ def _stream(stream=None):
 
 def _check_input(A: torch.Tensor):
     if not A.is_cuda:
-        raise ValueError("A must be a CUDA tensor (the library has no CPU path)")
+        raise ValueError("inputs must be CUDA tensors (the library has no CPU path)")
     if A.dtype != torch.float64:
-        raise ValueError("A must be float64")
+        raise ValueError("inputs must be float64")
+    if A.dim() != 2:
+        raise ValueError("inputs must be matrices")
 
 
 def default_panel(n: int) -> int:
@@ -143,6 +145,12 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
 
 def backward(Q: torch.Tensor, R: torch.Tensor, dQ: torch.Tensor | None, dR: torch.Tensor | None, stream=None):
     """Abar for A = QR: M = R Rbar^T - Qbar^T Q; Abar = (Qbar + Q copyltu(M)) R^{-T}."""
+    for t in (Q, R, dQ, dR):
+        if t is not None:
+            _check_input(t)
+    if R.shape != (Q.shape[1], Q.shape[1]) or (dQ is not None and dQ.shape != Q.shape) or (
+            dR is not None and dR.shape != R.shape):
+        raise ValueError("backward: Q (m x n), R (n x n), dQ like Q, dR like R")
     L = load()
     m, n = Q.shape
     Qc, Rc = colmajor(Q), colmajor(R)

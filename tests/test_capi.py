@@ -58,6 +58,15 @@ def test_no_cpu_fallback():
 
     with pytest.raises(ValueError):
         P.factor(torch.zeros(10, 2, dtype=torch.float64))
+    # every entry point refuses host tensors before anything reaches the library
+    Q, R = torch.zeros(10, 2, dtype=torch.float64), torch.eye(2, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        P.backward(Q, R, Q, R)
+    with pytest.raises(ValueError):
+        P.factor_batched([Q])
+    with pytest.raises(ValueError):
+        P.qr_batched([Q], 1)
+    assert P.factor_batched([]) == [] and P.qr_batched([]) == []
 
 
 def test_product_path_does_not_import_the_oracle():
