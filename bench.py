@@ -36,8 +36,8 @@ METRIC = "mCQR2GS FP64 TFLOP/s; batched QR/s vs looped; at ‖I−QᵀQ‖_F≤1
 M_FULL, N_FULL, KAPPA_FULL, SEED_FULL = 1 << 23, 1024, 1e15, 1002
 PANEL_CANDIDATES = (64, 128, 256)
 N_SM = 152
-FP64_FLOP_PER_CLK_SM = 4       # 2 DFMA per clock per SM (measured)
-SM_MAX_MHZ = 2070.0            # GB300 maximum SM clock
+# probe iterations: about 0.2-0.3 s per probe launch on GB300
+PROBE_ITERS = {"dfma": 100000, "dmma_m8n8k4": 30000, "dmma_m16n8k16": 4000}
 
 
 def parse():
@@ -431,7 +431,10 @@ def run_ours(args, dist, rank, world):
     for i in range(args.warmup):
         P.factor(A, b, out=(Q, R), workspace=ws, check=(i == 0), emulated=emu)
     torch.cuda.synchronize()
-    probe = P.probe_fp64_peak(20000)  # clocks are warm now
+    # FP64 peak microbenchmarks (clocks are warm now): DFMA and the two
+    # mma.sync .f64 shapes, each as flop per SM clock cycle
+    probes = {k: P.probe_fp64(k, it) for k, it in PROBE_ITERS.items()}
+    best_probe = max(probes.values(), key=lambda r: r["flop_per_clk_sm"])
     stream = torch.cuda.current_stream()
     barrier(dist)
     torch.cuda.synchronize()
@@ -458,12 +461,17 @@ def run_ours(args, dist, rank, world):
     # dominant kernel (largest device time) and its roofline
     dom = max(prof, key=lambda k: prof[k]["ms"])
     tot_ms = sum(v["ms"] for v in prof.values())
-    peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    # measured peak: the best probe's flop/clk/SM x SMs x the SM clock sampled in the timed region
+    clk_mhz = clocks["sm_mhz"] or best_probe["sm_mhz"]
+    peak = best_probe["flop_per_clk_sm"] * N_SM * clk_mhz * 1e6 / 1e12
     ach = prof[dom]["flops"] / (prof[dom]["ms"] * 1e-3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
     roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": update_traffic(m, n, b, dom, emu), "kernel": dom,
-                "peak_note": "FP64 FMA pipe: 152 SMs x 4 flop/clk x 2070 MHz (derived); "
-                             f"DFMA microbenchmark in this run: {probe / 1e3:.4f} TFLOP/s",
+                "peak_note": (f"measured: FP64 {best_probe['kind']} microbenchmark "
+                              f"{best_probe['flop_per_clk_sm']:.3f} flop/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz "
+                              "(median SM clock sampled during the timed region); probes: "
+                              + ", ".join(f"{k} {v['flop_per_clk_sm']:.3f} flop/clk/SM = {v['gflops'] / 1e3:.4f} "
+                                          f"TFLOP/s at {v['sm_mhz']:.0f} MHz" for k, v in probes.items())),
                 "share_of_device_time": prof[dom]["ms"] / tot_ms if tot_ms else None,
                 "launches": prof[dom]["launches"]}
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
@@ -537,7 +545,7 @@ def run_ours(args, dist, rank, world):
             "clocks": clocks,
             "accuracy": acc,
             "kernels": kernels,
-            "fp64_probe_tflops": probe / 1e3,
+            "fp64_probes": probes,
             **extras,
         }
         print(json.dumps(out), flush=True)

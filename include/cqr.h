@@ -11,8 +11,10 @@
  *   - All matrices are FP64, column-major, with leading dimension >= rows.
  *   - Matrix and workspace pointers are DEVICE pointers owned by the caller
  *     (except where an argument says "host").  The library never allocates
- *     device memory: the caller passes a workspace of at least the size the
- *     matching *_workspace_size() function returns, 256-byte aligned.
+ *     device memory itself: the caller passes a workspace of at least the
+ *     size the matching *_workspace_size() function returns, 256-byte
+ *     aligned, or passes workspace = NULL to have it taken from an allocator
+ *     the caller registered with cqr_set_allocator() (see there).
  *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and returns without synchronising.  Every launch is
  *     asynchronous and graph-capturable: no allocation, no host sync.
@@ -24,9 +26,9 @@
  *     cqr_read_status() (synchronous) after the stream work completes.
  *     Status codes: 0 = ok; j+1 (> 0) = breakdown at global column j of the
  *     factorisation; CQR_STATUS_TIMEOUT = a bounded wait inside a kernel
- *     (an mbarrier of the emulated products) expired.  After a breakdown,
- *     every later kernel of
- *     the same call returns immediately and Q, R are undefined.
+ *     (an mbarrier of the emulated products, bounded at 2 s) expired.  After
+ *     a breakdown or a timeout, every later kernel of the same call returns
+ *     immediately and Q, R are undefined.
  */
 #ifndef CQR_GB300_H
 #define CQR_GB300_H
@@ -90,6 +92,32 @@ enum cqr_variant {
 #define CQR_ERR_CUDA (-1000)
 #define CQR_STATUS_TIMEOUT (-2000)
 #define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
+#define CQR_ERR_ALLOC (-4000)
+
+/*
+ * Caller-registered allocator for calls made with workspace = NULL.
+ *   cqr_alloc_fn(bytes, stream, ctx) returns DEVICE memory of at least
+ *     `bytes`, 256-byte aligned, usable on `stream` (NULL = failure);
+ *   cqr_free_fn(ptr, bytes, stream, ctx) takes it back.
+ * A call with workspace = NULL (cqr_factor, cqr_backward,
+ * cqr_factor_batched) asks for exactly the *_workspace_size() bytes,
+ * enqueues its work, SYNCHRONISES `stream`, then frees the memory -- so any
+ * allocator works (cudaMalloc/cudaFree, a caching allocator, a pool), and
+ * the call is synchronous and cannot be captured into a CUDA graph.
+ * cqr_factor then returns the status word itself (0, breakdown column + 1,
+ * or CQR_STATUS_TIMEOUT) instead of leaving it in the workspace.  Without a
+ * registered allocator workspace = NULL is an argument error; an allocation
+ * that fails or is misaligned returns CQR_ERR_ALLOC.
+ */
+typedef void* (*cqr_alloc_fn)(size_t bytes, struct CUstream_st* stream, void* ctx);
+typedef void (*cqr_free_fn)(void* ptr, size_t bytes, struct CUstream_st* stream, void* ctx);
+
+/*
+ * cqr_set_allocator: registers (alloc, free, ctx) for every later
+ * workspace = NULL call of this process; (NULL, NULL) unregisters.
+ * Returns 0, -1 (free without alloc) or -2 (alloc without free).
+ */
+int cqr_set_allocator(cqr_alloc_fn alloc, cqr_free_fn free_fn, void* ctx);
 
 /* Largest panel width the library accepts (the one-CTA Cholesky keeps a
  * b x b Gram matrix in shared memory up to 128 and in L2 above).  CQR_CQR2
@@ -127,7 +155,10 @@ int cqr_default_panel(int64_t n);
  *              its strict lower triangle is zeroed; ldr >= n        (args 8, 9)
  *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD, CQR_ADAPTIVE,
  *              CQR_EMULATED                                          (arg 10)
- *   workspace  device buffer of ws_bytes >= cqr_workspace_size()    (args 11, 12)
+ *   workspace  device buffer of ws_bytes >= cqr_workspace_size(), or
+ *              NULL: taken from the registered allocator, the call
+ *              synchronises and returns the status word (see
+ *              cqr_set_allocator)                                  (args 11, 12)
  *   stream     CUDA stream                                          (arg 13)
  * Panel loop (Alg. 9): for each panel j the Gram W_j = A_j^T A_j (Alg. 1
  * step 1), the b x b Cholesky W_j = U^T U (step 2), the triangular solve
@@ -145,9 +176,14 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
  * start-up, code called back from within another framework's allocator or
  * memory pool, code with a no-allocation-after-initialisation rule.  The
  * paper has no counterpart; this is a library convenience.
- *   Arguments 1-10 as in cqr_factor.  There is no workspace argument: the
- *   scratch is a file-scope device array of CQR_NOALLOC_SCRATCH_BYTES (64 MiB)
- *   that every GPU which loads the library holds until the process exits.
+ *   Arguments 1-9 as in cqr_factor.  Argument 10 is a plain variant (enum
+ *   cqr_variant) without flags: CQR_LOOKAHEAD, CQR_ADAPTIVE and CQR_EMULATED
+ *   are refused with -10.  There is no workspace argument: the scratch is a
+ *   file-scope device array of CQR_NOALLOC_SCRATCH_BYTES (64 MiB) that every
+ *   GPU which loads the library holds until the process exits.  Under the
+ *   CUDA runtime's lazy module loading (the default) the array is created on
+ *   a device by the first cqr_factor_noalloc call there, so make that first
+ *   call during initialisation.
  *   status   DEVICE int*: receives the status word (0, breakdown column + 1)
  *            when the stream reaches the end of the call; NULL = not reported
  *            (arg 11)
@@ -192,7 +228,8 @@ size_t cqr_backward_workspace_size(int64_t m, int64_t n);
  *   dR, lddr   upstream gradient Rbar (n x n); NULL means zero;
  *              only its upper triangle influences the result        (args 9, 10)
  *   dA, ldda   output Abar (m x n); must not overlap the inputs     (args 11, 12)
- *   workspace, ws_bytes, stream  as in cqr_factor                  (args 13-15)
+ *   workspace, ws_bytes, stream  as in cqr_factor (NULL workspace:
+ *              registered allocator, synchronous, returns 0)      (args 13-15)
  * Uses the same Gram/projection, update and triangular-solve kernels as the
  * forward pass.  The status word is not used (R is assumed nonsingular).
  */
@@ -218,8 +255,12 @@ size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n,
  *   variant                as in cqr_factor                          (arg 9)
  *   status                 DEVICE int array of length batch: per-matrix
  *                          status codes as in cqr_factor              (arg 10)
- *   workspace, ws_bytes    >= cqr_batched_workspace_size()            (args 11, 12)
+ *   workspace, ws_bytes    >= cqr_batched_workspace_size(), or NULL
+ *                          (registered allocator; synchronous)        (args 11, 12)
  *   stream                 CUDA stream                               (arg 13)
+ * The host size arrays come first and the device-pointer arrays after
+ * them; Q_i and R_i take the leading dimensions lda_i and n_i, so there are
+ * no ldq / ldr arrays.
  * The matrices are distributed (largest work first) over a pool of
  * library-owned streams that are forked from `stream` and joined back into
  * it with events, so small grids, Cholesky islands and reductions of
@@ -233,15 +274,49 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
                        double* const* A, double* const* Q, double* const* R, int variant, int* status,
                        void* workspace, size_t ws_bytes, cqr_stream_t stream);
 
+/*
+ * cqr_test_arm_wait_expiry: test hook of the bounded waits (failure
+ * detection; not in the paper).  Every mbarrier wait inside the tensor-core
+ * kernels of CQR_EMULATED is bounded in time (2 s); on expiry the block
+ * records CQR_STATUS_TIMEOUT in the status word, waits (bounded) for its
+ * copies in flight, frees its tensor memory and returns, and every later
+ * kernel of the call returns at once.  This hook makes that path run: the
+ * NEXT launch of the chosen kernel withholds the copies of one stage, so
+ * the waits for it expire after `wait_ns`, and the hook disarms itself.
+ *   kernel   0 = the product kernel (Gram matrices, projections), 1 = the
+ *            update kernel, -1 = disarm                              (arg 1)
+ *   stage    first stage (per block) whose copies are withheld, >= 0  (arg 2)
+ *   wait_ns  bound of every wait of that launch, 1 .. 2e9             (arg 3)
+ * Host-side only (nothing is launched).  Returns 0, or -i for argument i.
+ */
+int cqr_test_arm_wait_expiry(int kernel, int stage, long long wait_ns);
+
 /* cqr_status_string: static description of a status or return code. */
 const char* cqr_status_string(int status);
 
 /*
  * cqr_probe_fp64_peak: measures this GPU's FP64 FMA throughput (DFMA chains
- * on every SM) for `iters` iterations and returns GFLOP/s (<= 0 on error).
- * Synchronous.  Used to state the FP64 roofline the kernels run against.
+ * on every SM, kind 0 of cqr_probe_fp64) for `iters` iterations and returns
+ * GFLOP/s (<= 0 on error).  Synchronous.
  */
 double cqr_probe_fp64_peak(int iters);
+
+/*
+ * cqr_probe_fp64: FP64 peak microbenchmarks, the denominators of the
+ * roofline fractions (measurement support; not in the paper).
+ *   kind   0 = DFMA on the CUDA cores (the pipe every native kernel here
+ *          uses); 1 = FP64 tensor cores, mma.sync m8n8k4 .f64; 2 = FP64
+ *          tensor cores, mma.sync m16n8k16 .f64                        (arg 1)
+ *   iters  iterations of the timed loop (about 1e5 gives ~0.1 s)      (arg 2)
+ *   gflops, flop_per_clk_sm, sm_mhz  HOST outputs (each may be NULL): the
+ *          throughput of the fastest of three single-wave launches, its
+ *          FLOPs per SM clock cycle (SM cycle counters, independent of the
+ *          clock the GPU ran at) and the effective SM clock, cycles / time
+ *                                                                  (args 3-5)
+ * Synchronous, on the legacy default stream; allocates nothing.  Returns 0,
+ * -1 for a bad kind, -2 for iters < 1, CQR_ERR_CUDA on a CUDA error.
+ */
+int cqr_probe_fp64(int kind, int iters, double* gflops, double* flop_per_clk_sm, double* sm_mhz);
 
 /*
  * Launch accounting and kernel timing (measurement support; not in the

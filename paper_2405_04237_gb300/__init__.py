@@ -24,8 +24,9 @@ from ._capi import CQRError, VARIANTS, load, status_string
 
 __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
-    "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "colmajor", "empty_colmajor",
+    "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "probe_fp64", "colmajor", "empty_colmajor",
     "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size", "qr_batched", "CQRBatchedFunction",
+    "use_torch_allocator",
 ]
 
 
@@ -70,6 +71,41 @@ def _check_input(A: torch.Tensor):
         raise ValueError("inputs must be float64")
     if A.dim() != 2:
         raise ValueError("inputs must be matrices")
+
+
+_torch_alloc_callbacks = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Register torch's CUDA caching allocator with cqr_set_allocator, for C
+    calls made with workspace = NULL (those calls synchronise their stream
+    before they free, so the caching allocator may reuse the block at once).
+    enable=False unregisters it."""
+    global _torch_alloc_callbacks
+    L = load()
+    if not enable:
+        rc = L.cqr_set_allocator(_capi.ALLOC_FN(), _capi.FREE_FN(), None)
+        _torch_alloc_callbacks = None
+        if rc != 0:
+            raise CQRError(rc, "cqr_set_allocator")
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          int(stream or 0)))
+        except Exception:  # the library sees NULL and returns CQR_ERR_ALLOC
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = (_capi.ALLOC_FN(_alloc), _capi.FREE_FN(_free))
+    rc = L.cqr_set_allocator(cbs[0], cbs[1], None)
+    if rc != 0:
+        raise CQRError(rc, "cqr_set_allocator")
+    _torch_alloc_callbacks = cbs  # keep the ctypes thunks alive while registered
 
 
 def default_panel(n: int) -> int:
@@ -330,9 +366,22 @@ class BatchedGraph:
         return self.out
 
 
-def probe_fp64_peak(iters: int = 4000) -> float:
+def probe_fp64_peak(iters: int = 20000) -> float:
     """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
     return float(load().cqr_probe_fp64_peak(int(iters)))
+
+
+PROBE_KINDS = {"dfma": 0, "dmma_m8n8k4": 1, "dmma_m16n8k16": 2}
+
+
+def probe_fp64(kind: str = "dfma", iters: int = 100000) -> dict:
+    """FP64 peak microbenchmark (cqr_probe_fp64): GFLOP/s, flop per clock per
+    SM (from the SM cycle counters) and the effective SM clock in MHz."""
+    g, f, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    rc = load().cqr_probe_fp64(PROBE_KINDS[kind], int(iters), ctypes.byref(g), ctypes.byref(f), ctypes.byref(c))
+    if rc != 0:
+        raise CQRError(rc, "cqr_probe_fp64")
+    return {"kind": kind, "gflops": g.value, "flop_per_clk_sm": f.value, "sm_mhz": c.value}
 
 
 def launch_count() -> int:

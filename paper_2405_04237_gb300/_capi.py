@@ -23,13 +23,16 @@ VARIANTS = {"mcqr2gs": MCQR2GS, "cqr2gs": CQR2GS, "cqr2": CQR2, "scqr3": SCQR3}
 ERR_CUDA = -1000
 STATUS_TIMEOUT = -2000
 ERR_NOALLOC_TOO_LARGE = -3000
+ERR_ALLOC = -4000
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTS = [
-    "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status",
+    "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status", "cqr_set_allocator",
     "cqr_backward_workspace_size", "cqr_backward", "cqr_batched_workspace_size",
-    "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak",
-    "cqr_factor_noalloc", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
+    "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak", "cqr_probe_fp64",
+    "cqr_factor_noalloc", "cqr_test_arm_wait_expiry", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
 ]
 KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "misc",
                   "batched"]
@@ -68,6 +71,7 @@ def load(build_if_missing: bool = True):
             "cqr_default_panel": (c_int, [i64]),
             "cqr_factor": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, sz, vp]),
             "cqr_read_status": (c_int, [vp, vp, PI]),
+            "cqr_set_allocator": (c_int, [ALLOC_FN, FREE_FN, vp]),
             "cqr_factor_noalloc": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, vp]),
             "cqr_backward_workspace_size": (sz, [i64, i64]),
             "cqr_backward": (c_int, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64, vp, sz, vp]),
@@ -75,6 +79,9 @@ def load(build_if_missing: bool = True):
             "cqr_factor_batched": (c_int, [c_int, P64, P64, P64, PI, PV, PV, PV, c_int, vp, vp, sz, vp]),
             "cqr_status_string": (ctypes.c_char_p, [c_int]),
             "cqr_probe_fp64_peak": (ctypes.c_double, [c_int]),
+            "cqr_probe_fp64": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
+            "cqr_test_arm_wait_expiry": (c_int, [c_int, c_int, ctypes.c_longlong]),
             "cqr_launch_count": (ctypes.c_ulonglong, []),
             "cqr_profile_enable": (c_int, [c_int]),
             "cqr_profile_disable": (c_int, []),

@@ -293,6 +293,44 @@ const Side* get_side() {
   return &g_side[dev];
 }
 
+// Caller-registered allocator for calls made with workspace == NULL.
+struct Allocator {
+  cqr_alloc_fn alloc = nullptr;
+  cqr_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+bool registered_allocator(Allocator* out) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  *out = g_alloc;
+  return out->alloc != nullptr;
+}
+
+// workspace == NULL: take `bytes` from the registered allocator, run `body`
+// on it, synchronise `st`, read the status word at offset 0 when asked, and
+// hand the memory back.  Returns body's nonzero code, CQR_ERR_ALLOC, a CUDA
+// error, or the status word (0 when not read).
+template <class F>
+int with_allocated_workspace(const Allocator& al, size_t bytes, cudaStream_t st, bool read_status, F&& body) {
+  void* ws = al.alloc(bytes, (cqr_stream_t)st, al.ctx);
+  if (!ws) return CQR_ERR_ALLOC;
+  if ((uintptr_t)ws & 255) {
+    al.free(ws, bytes, (cqr_stream_t)st, al.ctx);
+    return CQR_ERR_ALLOC;
+  }
+  int rc = body(ws);
+  int status = 0;
+  if (rc == 0 && read_status) {
+    if (cudaMemcpyAsync(&status, ws, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = CQR_ERR_CUDA;
+  }
+  // the memory goes back only once the stream has finished with it
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == 0) rc = CQR_ERR_CUDA;
+  al.free(ws, bytes, (cqr_stream_t)st, al.ctx);
+  return rc != 0 ? rc : status;
+}
+
 bool overlaps(const double* a, i64 lda, i64 m, i64 n, const double* b, i64 ldb) {
   const char* a0 = (const char*)a;
   const char* a1 = (const char*)(a + (n - 1) * lda + m);
@@ -304,6 +342,16 @@ bool overlaps(const double* a, i64 lda, i64 m, i64 n, const double* b, i64 ldb) 
 }  // namespace
 
 extern "C" {
+
+int cqr_set_allocator(cqr_alloc_fn alloc, cqr_free_fn free_fn, void* ctx) {
+  if (!alloc && free_fn) return -1;
+  if (alloc && !free_fn) return -2;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return 0;
+}
 
 int cqr_default_panel(int64_t n) {
   if (n <= 0) return 0;
@@ -350,11 +398,18 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   if (Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
   if (!R) return -8;
   if (ldr < n) return -9;
-  if (!workspace || ((uintptr_t)workspace & 255)) return -11;
   if ((emulated || adaptive) && variant != CQR_MCQR2GS) return -10;
   const Layout L = make_layout(m, n, b, variant, emulated);
-  if (ws_bytes < L.total) return -12;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!workspace) {
+    Allocator al;
+    if (!registered_allocator(&al)) return -11;
+    return with_allocated_workspace(al, L.total, st, true, [&](void* ws) {
+      return cqr_factor(m, n, A, lda, panel_b, Q, ldq, R, ldr, variant_flags, ws, L.total, stream);
+    });
+  }
+  if ((uintptr_t)workspace & 255) return -11;
+  if (ws_bytes < L.total) return -12;
   Work w = bind(workspace, L);
   if (emulated) w.oz = (char*)workspace + L.oz;
   cudaGetLastError();  // clear stale errors from earlier, unrelated calls
@@ -409,9 +464,17 @@ int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const doubl
   if (!dA) return -11;
   if (ldda < m) return -12;
   if (overlaps(dA, ldda, m, n, Q, ldq) || (dQ && overlaps(dA, ldda, m, n, dQ, lddq))) return -11;
-  if (!workspace || ((uintptr_t)workspace & 255)) return -13;
-  if (ws_bytes < cqr_backward_workspace_size(m, n)) return -14;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!workspace) {
+    Allocator al;
+    if (!registered_allocator(&al)) return -13;
+    const size_t need = cqr_backward_workspace_size(m, n);
+    return with_allocated_workspace(al, need, st, false, [&](void* ws) {
+      return cqr_backward(m, n, Q, ldq, R, ldr, dQ, lddq, dR, lddr, dA, ldda, ws, need, stream);
+    });
+  }
+  if ((uintptr_t)workspace & 255) return -13;
+  if (ws_bytes < cqr_backward_workspace_size(m, n)) return -14;
   char* p = (char*)workspace;
   size_t off = 0;
   double* G = (double*)(p + off);
@@ -527,8 +590,6 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
   if (!A || !Q || !R) return -6;
   if (variant != CQR_MCQR2GS && variant != CQR_CQR2GS) return -9;
   if (!status) return -10;
-  if (!workspace || ((uintptr_t)workspace & 255)) return -11;
-  if (ws_bytes < cqr_batched_workspace_size(batch, m, n, panel_b, variant)) return -12;
   for (int i = 0; i < batch; ++i) {
     if (m[i] < 1 || n[i] < 1 || m[i] < n[i] || lda[i] < m[i]) return -2;
     const int b = resolve_panel(n[i], panel_b[i], variant);
@@ -536,6 +597,16 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
     if (!A[i] || !Q[i] || !R[i]) return -6;
     if (Q[i] != A[i] && overlaps(A[i], lda[i], m[i], n[i], Q[i], lda[i])) return -7;
   }
+  if (!workspace) {
+    Allocator al;
+    if (!registered_allocator(&al)) return -11;
+    const size_t need = cqr_batched_workspace_size(batch, m, n, panel_b, variant);
+    return with_allocated_workspace(al, need, (cudaStream_t)stream, false, [&](void* ws) {
+      return cqr_factor_batched(batch, m, n, lda, panel_b, A, Q, R, variant, status, ws, need, stream);
+    });
+  }
+  if ((uintptr_t)workspace & 255) return -11;
+  if (ws_bytes < cqr_batched_workspace_size(batch, m, n, panel_b, variant)) return -12;
   std::lock_guard<std::mutex> lk(g_pool_mu);
   StreamPool* pool = get_pool();
   if (!pool) return CQR_ERR_CUDA;
@@ -600,8 +671,9 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
 // framework's allocator or memory pool, or code with a rule that nothing
 // allocates after initialisation.  For them the scratch that cqr_factor()
 // takes as a caller-supplied workspace lives in this file-scope device array
-// instead: it is created when the library is loaded and held by every GPU
-// that loads the library until the process exits.
+// instead.  Every GPU that loads the library holds it until the process
+// exits; under the runtime's lazy module loading it is created on a device
+// by the first call there (the symbol lookup below loads the module).
 namespace {
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[CQR_NOALLOC_SCRATCH_BYTES];
@@ -664,11 +736,23 @@ const char* cqr_status_string(int status) {
   if (status == CQR_ERR_NOALLOC_TOO_LARGE)
     return "cqr_factor_noalloc: the factorisation needs more scratch than the fixed CQR_NOALLOC_SCRATCH_BYTES array";
   if (status == CQR_ERR_CUDA) return "a CUDA launch or copy failed";
+  if (status == CQR_ERR_ALLOC)
+    return "workspace = NULL: the allocator registered with cqr_set_allocator returned no 256-byte aligned memory";
   if (status == CQR_STATUS_TIMEOUT) return "a bounded wait inside a kernel expired";
   if (status > 0) return "Cholesky breakdown: the Gram matrix is not numerically positive definite (status = column + 1)";
   return "invalid argument (status = -(argument position))";
 }
 
-double cqr_probe_fp64_peak(int iters) { return probe_fp64(iters > 0 ? iters : 4000); }
+double cqr_probe_fp64_peak(int iters) {
+  double g = 0.0;
+  return probe_fp64(0, iters > 0 ? iters : 20000, &g, nullptr, nullptr) == 0 ? g : -1.0;
+}
+
+int cqr_probe_fp64(int kind, int iters, double* gflops, double* flop_per_clk_sm, double* sm_mhz) {
+  if (kind < 0 || kind > 2) return -1;
+  if (iters < 1) return -2;
+  const int rc = probe_fp64(kind, iters, gflops, flop_per_clk_sm, sm_mhz);
+  return rc == 0 ? 0 : (rc == -1 ? -2 : CQR_ERR_CUDA);
+}
 
 }  // extern "C"

@@ -106,8 +106,10 @@ cudaError_t backward_middle(int n, const double* T, const double* G, double* M, 
 // Reciprocals of the diagonal of R.
 cudaError_t diag_reciprocal(int n, const double* R, i64 ldr, double* rinv, cudaStream_t st);
 
-// FP64 FMA throughput probe (GFLOP/s).
-double probe_fp64(int iters);
+// FP64 throughput probes (k_probe.cu): kind 0 DFMA, 1 mma.sync m8n8k4 .f64,
+// 2 mma.sync m16n8k16 .f64.  Synchronous; returns 0 and GFLOP/s, flop per
+// clock per SM (from the SM cycle counters) and the effective SM clock.
+int probe_fp64(int kind, int iters, double* gflops, double* flop_per_clk_sm, double* sm_mhz);
 
 // ---------------------------------------------------------------------------
 // Launch accounting (prof.cu).  Every launch is wrapped in prof_begin /

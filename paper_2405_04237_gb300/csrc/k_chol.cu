@@ -141,21 +141,6 @@ __global__ void diag_reciprocal_kernel(int n, const double* R, i64 ldr, double* 
   if (j < n) rinv[j] = 1.0 / R[j + (i64)j * ldr];
 }
 
-__device__ double g_probe_sink;
-
-__global__ void probe_kernel(int iters, double a, double b) {
-  double acc[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) acc[i] = threadIdx.x * 1e-3 + i;
-  for (int it = 0; it < iters; ++it)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = fma(acc[i], a, b);
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) s += acc[i];
-  if (s == 1.2345e-300) g_probe_sink = s;  // keeps the chains live
-}
-
 }  // namespace
 
 cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* rinv, int col0, int* status,
@@ -194,40 +179,6 @@ cudaError_t diag_reciprocal(int n, const double* R, i64 ldr, double* rinv, cudaS
   diag_reciprocal_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, R, ldr, rinv);
   prof_end(kMisc, (double)n, st);
   return cudaGetLastError();
-}
-
-double probe_fp64(int iters) {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  const int blocks = sms * 4, threads = 256;
-  // warm-up long enough for the clocks to settle, then the best of three
-  for (int w = 0; w < 3; ++w) {
-    prof_begin(kMisc, 0);
-    probe_kernel<<<blocks, threads>>>(iters, 0.999999, 1e-7);
-    prof_end(kMisc, 0.0, 0);
-  }
-  float best = 0.f;
-  cudaError_t err = cudaSuccess;
-  for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
-    cudaEventRecord(e0);
-    prof_begin(kMisc, 0);
-    probe_kernel<<<blocks, threads>>>(iters, 0.999999, 1e-7);
-    prof_end(kMisc, 0.0, 0);
-    cudaEventRecord(e1);
-    err = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms > 0.f && (best == 0.f || ms < best)) best = ms;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (err != cudaSuccess || best <= 0.f) return -1.0;
-  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
-  return flops / (best * 1e-3) / 1e9;
 }
 
 }  // namespace cqr

@@ -50,9 +50,15 @@
 // combines levels 13..19 and 20..26 exactly in 64-bit integers (below 2^49),
 // builds the two scaled doubles with integer operations and adds them (one
 // rounding), so the FP64 pipe does one operation per element (two for an
-// update, which subtracts the tile from C).  Every wait is bounded; on
-// expiry the block records CQR_STATUS_TIMEOUT, waits (bounded) for its
-// copies in flight, frees its TMEM and returns.
+// update, which subtracts the tile from C).  Every wait is bounded in time
+// (kWaitNs of the global nanosecond timer, 2 s: a stage arrives within
+// microseconds); on expiry the block records CQR_STATUS_TIMEOUT, waits
+// (bounded) for its copies in flight, frees its TMEM and returns.  A
+// one-shot host-side test hook (cqr_test_arm_wait_expiry) makes the next
+// launch of one of the two kernels withhold the copies of one stage, with a
+// short bound, so that the expiry path runs and can be checked.
+#include <mutex>
+
 #include "cqr_common.cuh"
 #include "cqr.h"
 
@@ -88,7 +94,7 @@ static_assert(kLevelLo == 13 && kLevels == 14, "the MMA schedule and the two gro
 // 4-5 = 1), A and B e4m3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 =
 // 0), M >> 4 at bits 24-28; N >> 3 goes to bits 17-22.
 constexpr uint32_t kTcIdescM = (1u << 4) | ((uint32_t)(kTcM >> 4) << 24);
-constexpr long kTcSpin = 1L << 24;  // bound of every mbarrier wait (iterations of try_wait)
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait (ns of %globaltimer)
 
 inline int round_up(int x, int t) { return (x + t - 1) / t * t; }
 
@@ -293,11 +299,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait; false when the bound expired.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long it = 0; it < kTcSpin; ++it)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait bounded in time; false when the bound (ns) expired first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -401,6 +415,8 @@ struct OzArgs {
   double* C;          // update: C (ldc) of the chunk's first row
   i64 ldc;
   int* status;
+  unsigned long long wait_ns;  // bound of every mbarrier wait (kWaitNs unless the test hook is armed)
+  int withhold;                // test hook: the producer issues no copies from this stage on (-1: none)
 };
 
 // Projections: one 128 x 32 tile of one sub-chunk per block, grid
@@ -454,11 +470,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
     int issued = 0;
     for (int st = 0; st < nst; ++st) {
       const int slot = st % kTcRing;
-      if (st >= kTcRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((st / kTcRing - 1) & 1))) {
+      if (st >= kTcRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((st / kTcRing - 1) & 1), a.wait_ns)) {
         atomicExch(&give_up, 1);
         break;
       }
-      if (*(volatile int*)&give_up) break;
+      if (*(volatile int*)&give_up || st == a.withhold) break;
       const uint32_t fb = smem_u32(&full_bar[slot]);
       const uint32_t sa = smem_u32(ring + slot * kTcStageBytes), sb = sa + kTcABytes;
       mbar_expect_tx(fb, kTcStageBytes);
@@ -474,12 +490,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
     }
     // before leaving, every issued copy must have landed (bounded)
     for (int st = issued - kTcRing < 0 ? 0 : issued - kTcRing; st < issued; ++st)
-      mbar_wait(smem_u32(&full_bar[st % kTcRing]), (uint32_t)((st / kTcRing) & 1));
+      mbar_wait(smem_u32(&full_bar[st % kTcRing]), (uint32_t)((st / kTcRing) & 1), a.wait_ns);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: the 22 instructions of each stage (the 105 pairs, level L = i + j into region L - 11)
     for (int st = 0; st < nst; ++st) {
       const int slot = st % kTcRing;
-      if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((st / kTcRing) & 1))) {
+      if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((st / kTcRing) & 1), a.wait_ns)) {
         atomicExch(&give_up, 1);
         break;
       }
@@ -499,7 +515,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) ozaki_tc_kernel(OzArgs a) {
     tc_commit(smem_u32(&done_bar));  // arrives when every MMA issued above has completed
   }
   __syncwarp();
-  const bool done = mbar_wait(smem_u32(&done_bar), 0);
+  const bool done = mbar_wait(smem_u32(&done_bar), 0, a.wait_ns);
   // one decision for the whole block, and converged warps for tcgen05.ld
   const int failed = __syncthreads_or(!done || *(volatile int*)&give_up);
   tc_fence_after();
@@ -612,12 +628,12 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
         const uint8_t* gy = a.py + (i64)(T % a.tiles_q) * kStagesPerSub * kTcBBytes;
         for (int st = 0; st < nst; ++st) {
           const int slot = g % kUpRing;
-          if (g >= kUpRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((g / kUpRing - 1) & 1))) {
+          if (g >= kUpRing && !mbar_wait(smem_u32(&empty_bar[slot]), (uint32_t)((g / kUpRing - 1) & 1), a.wait_ns)) {
             atomicExch(&give_up, 1);
             stop = true;
             break;
           }
-          if (*(volatile int*)&give_up) {
+          if (*(volatile int*)&give_up || g == a.withhold) {
             stop = true;
             break;
           }
@@ -631,21 +647,22 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
       }
       // every issued copy must have landed before the block leaves (bounded)
       for (int h = g - kUpRing < 0 ? 0 : g - kUpRing; h < g; ++h)
-        mbar_wait(smem_u32(&full_bar[h % kUpRing]), (uint32_t)((h / kUpRing) & 1));
+        mbar_wait(smem_u32(&full_bar[h % kUpRing]), (uint32_t)((h / kUpRing) & 1), a.wait_ns);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       int g = 0, k = 0;
       bool stop = false;
       for (int T = blockIdx.x; T < ntiles && !stop; T += gridDim.x, ++k) {
-        if (k >= 1 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((k - 1) & 1))) {
+        if (k >= 1 && !mbar_wait(smem_u32(&acc_empty), (uint32_t)((k - 1) & 1), a.wait_ns)) {
           atomicExch(&give_up, 1);
           break;
         }
         tc_fence_after();
         for (int st = 0; st < nst; ++st) {
           const int slot = g % kUpRing;
-          if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((g / kUpRing) & 1)) || *(volatile int*)&give_up) {
+          if (!mbar_wait(smem_u32(&full_bar[slot]), (uint32_t)((g / kUpRing) & 1), a.wait_ns) ||
+              *(volatile int*)&give_up) {
             atomicExch(&give_up, 1);
             stop = true;
             break;
@@ -666,7 +683,7 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
         tc_commit(smem_u32(&acc_full));
       }
       tc_commit(smem_u32(&mma_done));  // every MMA issued above has completed when this arrives
-      mbar_wait(smem_u32(&mma_done), 0);
+      mbar_wait(smem_u32(&mma_done), 0, a.wait_ns);
     }
   } else {
     // epilogue: TMEM lane quarter qw, tile row r
@@ -675,7 +692,7 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
     int k = 0;
     for (int T = blockIdx.x; T < ntiles; T += gridDim.x, ++k) {
       const int p0 = (T / a.tiles_q) * kTcM, q0 = (T % a.tiles_q) * kTcN;
-      const bool ok = mbar_wait(smem_u32(&acc_full), (uint32_t)(k & 1));
+      const bool ok = mbar_wait(smem_u32(&acc_full), (uint32_t)(k & 1), a.wait_ns);
       if (!__all_sync(0xffffffffu, ok) || *(volatile int*)&give_up) {
         atomicExch(&give_up, 1);
         break;
@@ -769,6 +786,25 @@ void tc_attr() {
   }
 }
 
+// One-shot test hook of the bounded waits (cqr_test_arm_wait_expiry): the
+// next launch of kernel `g_fault_kernel` (0 = ozaki_tc_kernel, 1 =
+// ozaki_tc_update_kernel) gets the armed stage to withhold and wait bound,
+// then the hook disarms itself.
+std::mutex g_fault_mu;
+int g_fault_kernel = -1, g_fault_stage = -1;
+unsigned long long g_fault_ns = 0;
+
+void take_fault(int kernel, OzArgs& a) {
+  a.wait_ns = kWaitNs;
+  a.withhold = -1;
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  if (g_fault_kernel == kernel) {
+    a.wait_ns = g_fault_ns;
+    a.withhold = g_fault_stage;
+    g_fault_kernel = -1;
+  }
+}
+
 // Rows per update chunk: the X planes of one chunk take about 1 GiB.
 inline i64 oz_nn_rows(int nst) {
   i64 rows = ((i64)1 << 30) / ((i64)kPlanes * kStage * nst);
@@ -849,6 +885,7 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
     a.s_off = (int)(r0 / kSub);
     a.part = part;
     a.status = const_cast<int*>(status);
+    take_fault(0, a);
     prof_begin(kProjection, st);
     ozaki_tc_kernel<<<dim3((unsigned)tiles_q, (unsigned)tiles_p, (unsigned)nsub), kTcThreads, kTcSmem, st>>>(a);
     prof_end(kProjection, 2.0 * (double)(nsub * kSub < m - r0 ? nsub * kSub : m - r0) * p * q, st);
@@ -918,6 +955,7 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
       a.C = C + r0;
       a.ldc = ldc;
       a.status = const_cast<int*>(status);
+      take_fault(1, a);
       const int ntiles = (rws / kTcM) * tiles_q;
       prof_begin(kUpdate, st);
       ozaki_tc_update_kernel<<<(unsigned)(ntiles < kSMs ? ntiles : kSMs), kUpThreads, kUpSmem, st>>>(a, ntiles);
@@ -928,3 +966,19 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
 }
 
 }  // namespace cqr
+
+extern "C" int cqr_test_arm_wait_expiry(int kernel, int stage, long long wait_ns) {
+  if (kernel < -1 || kernel > 1) return -1;
+  if (kernel == -1) {  // disarm
+    std::lock_guard<std::mutex> lk(cqr::g_fault_mu);
+    cqr::g_fault_kernel = -1;
+    return 0;
+  }
+  if (stage < 0) return -2;
+  if (wait_ns < 1 || wait_ns > (long long)cqr::kWaitNs) return -3;
+  std::lock_guard<std::mutex> lk(cqr::g_fault_mu);
+  cqr::g_fault_kernel = kernel;
+  cqr::g_fault_stage = stage;
+  cqr::g_fault_ns = (unsigned long long)wait_ns;
+  return 0;
+}

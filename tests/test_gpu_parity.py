@@ -105,9 +105,13 @@ def test_parity_cqr2(cuda_lib, oracle, m, n):
     check_against_oracle(cuda_lib, oracle, A, n, "cqr2", 1e5)
 
 
-def test_parity_scqr3(cuda_lib, oracle):
-    A = make_test_matrix(20000, 48, 1e12, seed=1300)
-    check_against_oracle(cuda_lib, oracle, A, 48, "scqr3", 1e12)
+@pytest.mark.parametrize("kappa", [1e3, 1e6, 1e12])
+def test_parity_scqr3(cuda_lib, oracle, kappa):
+    """Shifted CholeskyQR3 (Alg. 5): the shift s = sqrt(m) u ||A||_F^2 (Alg. 4)
+    acts at every kappa, so the element-wise comparison at kappa <= 1e6 binds
+    the shifted first pass; at 1e12 only the norms bind."""
+    A = make_test_matrix(20000, 48, kappa, seed=1300)
+    check_against_oracle(cuda_lib, oracle, A, 48, "scqr3", kappa)
 
 
 def test_square_and_single_column(cuda_lib, oracle):
@@ -146,6 +150,20 @@ def test_lookahead_is_bitwise_identical(cuda_lib, variant, b):
     Q1, R1 = gpu_factor(cuda_lib, A, b, variant)
     Q2, R2 = gpu_factor(cuda_lib, A, b, variant, lookahead=True)
     assert np.array_equal(Q1, Q2) and np.array_equal(R1, R2)
+
+
+@pytest.mark.parametrize("variant,b,kappa", [("mcqr2gs", 16, 1e5), ("cqr2gs", 8, 1e5), ("mcqr2gs", 24, 1e15)])
+def test_lookahead_against_oracle(cuda_lib, oracle, variant, b, kappa):
+    """The look-ahead schedule against the oracle's plain Alg. 9 / Alg. 7
+    (not only against the GPU's default schedule): element-wise at 1e5,
+    norms at 1e15."""
+    A = make_test_matrix(40001, 96, kappa, seed=1505)
+    Qg, Rg = gpu_factor(cuda_lib, A, b, variant, lookahead=True)
+    Qo, Ro = oracle_factor(oracle, A, b, variant)
+    assert np.all(np.tril(Rg, -1) == 0) and np.all(np.diag(Rg) > 0)
+    assert orth_err(Qg) <= ORTH_TOL and resid(A, Qg, Rg) <= RES_TOL
+    if kappa <= 1e6:
+        assert rel_diff(Rg, Ro) <= R_TOL and np.abs(Qg - Qo).max() <= Q_TOL
 
 
 @pytest.mark.parametrize("kappa", [1.0, 1e10])

@@ -1,25 +1,25 @@
 """Full-size checks.
 
-1. The tall-skinny weak-scaling shape: m = 2^22, n = 256,
-b in {32, 64}, kappa in {1e15, 1e5}, the paper's test matrices (Sec. 2.2
-construction, generated on the GPU), mCQR2GS (Alg. 9) and CQR2GS (Alg. 7).
-
-The oracle would need minutes per factorisation here, so this file checks
-properties that hold at any size, each against something independent of
-this library:
+1. The tall-skinny weak-scaling shape: m = 2^22, n = 256, b in {32, 64},
+kappa in {1e15, 1e5}, the paper's test matrices (Sec. 2.2 construction,
+generated on the GPU), mCQR2GS (Alg. 9) and CQR2GS (Alg. 7).  Every
+(kappa, variant, b) is its own case.  Each case checks:
   * status 0, R upper triangular with a positive diagonal;
   * ||I - Q^T Q||_F <= 1e-13 and ||A - Q R||_F / ||A||_F <= 1e-14 (torch
-    FP64 GEMMs);
-  * kappa = 1e5: R within 1e-11 (relative, Frobenius) of the R factor of
-    torch.linalg.qr (LAPACK-style Householder on the GPU), sign-normalised
-    to a positive diagonal -- the R of a full-rank matrix with positive
-    diagonal is unique;
-  * kappa = 1e5: on 4096 sampled rows, Q equals A R^{-1} row by row
-    (triangular solve on the host, scipy) within 100 kappa u of max|Q|.
+    FP64 GEMMs over row chunks);
+  * kappa = 1e5, against the CPU oracle run on the same matrix (the plain
+    Alg. 9 / Alg. 7, about 1.1 TFLOP, 20-30 s on 16 host cores):
+    ||R_gpu - R_oracle||_F / ||R_oracle||_F <= 1e-11 and, on 4096 seeded
+    sampled rows, max |Q_gpu - Q_oracle| <= 1e-11 -- the tolerances of the
+    small-size parity tests;
+  * kappa = 1e5, as a second reference outside this library: R within
+    1e-11 of the R factor of torch.linalg.qr (Householder) sign-normalised
+    to a positive diagonal (the R of a full-rank matrix with positive
+    diagonal is unique), and on the sampled rows Q = A R^{-1} (host solve)
+    within 100 kappa u of max|Q|.
 CQR2GS at kappa = 1e15 runs with 8 panels (b = 32) only: the paper finds
 that CQR2GS needs about ten panels there (Sec. 5.3, Fig. 3); with 4 panels
-the oracle reaches only 1.7e-12 orthogonality at 2^18 x 256.  Its
-orthogonality bound is therefore 1e-12 (the oracle: 1.0e-14 at 2^18 rows).
+the oracle reaches only 1.7e-12 orthogonality at 2^18 x 256.
 
 2. The differentiable batch: 64 matrices, m uniform in [10^4, 10^5], n = 64,
 kappa = 1e4, b = 16, through qr_batched (one batched forward call, one
@@ -37,6 +37,11 @@ pytestmark = pytest.mark.gpu
 M, N = 1 << 22, 256
 SEED = 1001
 U = 2.0 ** -53
+R_TOL, Q_TOL, ORTH_TOL, RES_TOL = 1e-11, 1e-11, 1e-13, 1e-14
+SAMPLE_ROWS, SAMPLE_SEED = 4096, 7
+
+CASES = [(1e15, "mcqr2gs", 32), (1e15, "mcqr2gs", 64), (1e15, "cqr2gs", 32),
+         (1e5, "mcqr2gs", 32), (1e5, "mcqr2gs", 64), (1e5, "cqr2gs", 32), (1e5, "cqr2gs", 64)]
 
 
 def norms(A, Q, R, chunk=1 << 20):
@@ -58,50 +63,72 @@ def sign_normalised_r(A):
     return d[:, None] * R
 
 
-def rows_match_solve(A, Q, R, kappa, count=4096, seed=7):
-    """max |Q_s - A_s R^{-1}| over sampled rows, and its bound 100 kappa u max|Q_s|."""
-    solve_triangular = pytest.importorskip("scipy.linalg").solve_triangular
-
-    rng = np.random.default_rng(seed)
-    rows = torch.from_numpy(np.sort(rng.choice(A.shape[0], count, replace=False))).to(A.device)
-    As = A.index_select(0, rows).cpu().numpy()
-    Qs = Q.index_select(0, rows).cpu().numpy()
-    X = solve_triangular(R.cpu().numpy(), As.T, trans="T", lower=False).T
-    return np.abs(X - Qs).max(), 100.0 * kappa * U * np.abs(Qs).max()
+def sample_rows(m):
+    rng = np.random.default_rng(SAMPLE_SEED)
+    return np.sort(rng.choice(m, SAMPLE_ROWS, replace=False))
 
 
-def check_factorisation(A, Q, R, kappa, variant, b, R_ref=None):
-    Rc = R.cpu().numpy()
-    assert np.all(np.tril(Rc, -1) == 0) and np.all(np.diag(Rc) > 0), (variant, b, kappa)
-    orth, res = norms(A, Q, R)
-    bound = 1e-12 if (variant == "cqr2gs" and kappa > 1e8) else 1e-13
-    assert orth <= bound, (variant, b, kappa, orth)
-    assert res <= 1e-14, (variant, b, kappa, res)
-    if R_ref is not None:
-        rd = (torch.linalg.norm(R - R_ref) / torch.linalg.norm(R_ref)).item()
-        assert rd <= 1e-11, (variant, b, kappa, rd)
-        err, tol = rows_match_solve(A, Q, R, kappa)
-        assert err <= tol, (variant, b, kappa, err, tol)
+@pytest.fixture(scope="module")
+def full_size_matrix():
+    """kappa -> the GPU-generated A (one kappa held at a time, kept for the
+    cases of that kappa), its host copy for the oracle and torch's R
+    (kappa <= 1e6 only).  Released when the module's tests are done."""
+    cache = {}
+
+    def get(kappa):
+        if kappa not in cache:
+            from testmatrices import make_test_matrix_cuda
+
+            cache.clear()
+            torch.cuda.empty_cache()
+            A = make_test_matrix_cuda(M, N, kappa, SEED)
+            entry = {"A": A}
+            if kappa <= 1e6:
+                entry["R_torch"] = sign_normalised_r(A)
+                entry["A_host"] = A.cpu().numpy()  # column-major (Fortran-order) host copy
+            cache[kappa] = entry
+        return cache[kappa]
+
+    yield get
+    cache.clear()
+    torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("kappa", [1e15, 1e5])
-def test_full_size_tall_skinny(cuda_lib, kappa):
-    from testmatrices import make_test_matrix_cuda
-
+@pytest.mark.parametrize("kappa,variant,b", CASES)
+def test_full_size_tall_skinny(cuda_lib, oracle, full_size_matrix, kappa, variant, b):
     P = cuda_lib
-    A = make_test_matrix_cuda(M, N, kappa, SEED)
-    R_ref = sign_normalised_r(A) if kappa <= 1e6 else None
+    mat = full_size_matrix(kappa)
+    A = mat["A"]
     Q = P.empty_colmajor(M, N, "cuda")
     R = P.empty_colmajor(N, N, "cuda")
-    cases = [("mcqr2gs", 32), ("mcqr2gs", 64), ("cqr2gs", 32)] + ([("cqr2gs", 64)] if kappa <= 1e8 else [])
-    for variant, b in cases:
-        ws = torch.empty(P.workspace_size(M, N, b, variant), dtype=torch.uint8, device="cuda")
-        P.factor(A, b, variant, out=(Q, R), workspace=ws)  # raises on a nonzero status
-        torch.cuda.synchronize()
-        check_factorisation(A, Q, R, kappa, variant, b, R_ref)
-        del ws
-    del A, Q, R, R_ref
-    torch.cuda.empty_cache()
+    ws = torch.empty(P.workspace_size(M, N, b, variant), dtype=torch.uint8, device="cuda")
+    P.factor(A, b, variant, out=(Q, R), workspace=ws)  # raises on a nonzero status
+    torch.cuda.synchronize()
+    del ws
+    Rc = R.cpu().numpy()
+    assert np.all(np.tril(Rc, -1) == 0) and np.all(np.diag(Rc) > 0)
+    orth, res = norms(A, Q, R)
+    assert orth <= ORTH_TOL, orth
+    assert res <= RES_TOL, res
+    if kappa > 1e6:
+        return  # element-wise parity is unpinned here: the forward error grows like kappa u
+    rows = sample_rows(M)
+    idx = torch.from_numpy(rows).to(A.device)
+    Qs = Q.index_select(0, idx).cpu().numpy()
+    # the oracle on the same matrix
+    Qo, Ro = (oracle.mcqr2gs if variant == "mcqr2gs" else oracle.cqr2gs)(mat["A_host"], b)
+    rd = np.linalg.norm(Rc - Ro) / np.linalg.norm(Ro)
+    qd = np.abs(Qs - Qo[rows]).max()
+    del Qo
+    assert rd <= R_TOL, rd
+    assert qd <= Q_TOL, qd
+    # a second reference outside this library: torch's Householder R and Q = A R^{-1} on the sampled rows
+    R_t = mat["R_torch"]
+    rt = (torch.linalg.norm(R - R_t) / torch.linalg.norm(R_t)).item()
+    assert rt <= R_TOL, rt
+    As = mat["A_host"][rows]
+    X = np.linalg.solve(Rc.T, As.T).T
+    assert np.abs(X - Qs).max() <= 100.0 * kappa * U * np.abs(Qs).max()
 
 
 def test_differentiable_batch_of_64(cuda_lib):

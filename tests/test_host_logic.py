@@ -170,6 +170,32 @@ def test_noalloc_argument_codes_and_limit(L):
     assert "CQR_NOALLOC_SCRATCH_BYTES" in P.status_string(_capi.ERR_NOALLOC_TOO_LARGE)
 
 
+def test_allocator_registration_codes(L):
+    """cqr_set_allocator: both callbacks or neither; with none registered, a
+    NULL workspace stays an argument error (nothing is allocated or run)."""
+    null_a, null_f = _capi.ALLOC_FN(), _capi.FREE_FN()
+    a = _capi.ALLOC_FN(lambda nbytes, stream, ctx: None)
+    f = _capi.FREE_FN(lambda ptr, nbytes, stream, ctx: None)
+    assert L.cqr_set_allocator(null_a, f, None) == -1
+    assert L.cqr_set_allocator(a, null_f, None) == -2
+    assert L.cqr_set_allocator(null_a, null_f, None) == 0
+    assert factor_rc(L, ws=0) == -11
+    assert L.cqr_backward(1000, 64, vp(Q_ADDR), 1000, vp(R_ADDR), 64, vp(0), 1000, vp(0), 64, vp(W_ADDR), 1000,
+                          vp(0), 0, vp(0)) == -13
+    assert "cqr_set_allocator" in P.status_string(_capi.ERR_ALLOC)
+
+
+def test_wait_expiry_hook_codes(L):
+    """The test hook of the bounded waits is host-side only: arming and
+    disarming launch nothing; its arguments are checked."""
+    assert L.cqr_test_arm_wait_expiry(2, 0, 1000) == -1
+    assert L.cqr_test_arm_wait_expiry(0, -1, 1000) == -2
+    assert L.cqr_test_arm_wait_expiry(0, 0, 0) == -3
+    assert L.cqr_test_arm_wait_expiry(1, 0, 3_000_000_000) == -3      # beyond the production bound
+    assert L.cqr_test_arm_wait_expiry(0, 1, 1_000_000) == 0
+    assert L.cqr_test_arm_wait_expiry(-1, 0, 1) == 0                  # disarm
+
+
 def test_status_strings():
     assert P.status_string(0) == "success"
     assert "breakdown" in P.status_string(17)
