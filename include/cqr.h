@@ -89,6 +89,23 @@ enum cqr_variant {
  * planes of one row chunk (about 1 GiB) and one FP64 partial per 4096 rows. */
 #define CQR_EMULATED 0x400
 
+/* Flag OR-ed into `variant` of cqr_factor and cqr_workspace_size (MCQR2GS
+ * only; not with CQR_EMULATED or CQR_LOOKAHEAD): adaptive panel width, the
+ * paper's remedy for a Cholesky breakdown -- a smaller b lowers every
+ * panel's condition number (Sec. 5.3-5.4, Eq. cond_bounds).  The first
+ * CholeskyQR of each panel (Alg. 9 step 1's first pass, step 6) is tested:
+ * the panel is rejected when its Cholesky factorisation breaks down or
+ * (max U_ii / min U_ii)^2 > 1/(64 u), u = 2^-53 (its Gram matrix within a
+ * factor 64 of numerical singularity).  A rejected panel is left untouched
+ * and retried with the largest divisor of b that is <= b/2; every later
+ * panel keeps the new width.  A one-column panel is never rejected (its
+ * breakdown is reported as usual).  With no rejection the result is bitwise
+ * that of the fixed width.  The decision is read on the host before each
+ * triangular solve, so the call SYNCHRONISES `stream` once per panel
+ * attempt and cannot be captured into a CUDA graph.  The final width is
+ * left in the workspace; read it with cqr_read_panel_width(). */
+#define CQR_HALVE 0x800
+
 #define CQR_ERR_CUDA (-1000)
 #define CQR_STATUS_TIMEOUT (-2000)
 #define CQR_ERR_NOALLOC_TOO_LARGE (-3000)
@@ -154,7 +171,7 @@ int cqr_default_panel(int64_t n);
  *   R, ldr     output n x n upper triangular with positive diagonal;
  *              its strict lower triangle is zeroed; ldr >= n        (args 8, 9)
  *   variant    enum cqr_variant, optionally | CQR_LOOKAHEAD, CQR_ADAPTIVE,
- *              CQR_EMULATED                                          (arg 10)
+ *              CQR_EMULATED, CQR_HALVE                               (arg 10)
  *   workspace  device buffer of ws_bytes >= cqr_workspace_size(), or
  *              NULL: taken from the registered allocator, the call
  *              synchronises and returns the status word (see
@@ -203,6 +220,14 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
 #define CQR_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int cqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
                        int64_t ldr, int variant, int* status, cqr_stream_t stream);
+
+/*
+ * cqr_read_panel_width: synchronises `stream`, then copies into *panel_b
+ * (host) the width of the last panel of the last CQR_HALVE call that used
+ * `workspace` (not written by calls without the flag, nor when the
+ * workspace was NULL).  Returns 0, -1 for a NULL argument, or CQR_ERR_CUDA.
+ */
+int cqr_read_panel_width(const void* workspace, cqr_stream_t stream, int* panel_b);
 
 /*
  * cqr_read_status: synchronises `stream`, then copies the status word of the

@@ -73,6 +73,7 @@ def _sigs():
         "or_cqrgs": (ctypes.c_int, [i64, i64, i64, dp, i64, dp, i64]),
         "or_cqr2gs": (ctypes.c_int, [i64, i64, i64, dp, i64, dp, i64]),
         "or_mcqr2gs": (ctypes.c_int, [i64, i64, i64, dp, i64, dp, i64, ctypes.c_int]),
+        "or_mcqr2gs_halving": (ctypes.c_int, [i64, i64, i64, dp, i64, dp, i64, ctypes.POINTER(i64)]),
         "or_backward": (None, [i64, i64, cdp, i64, cdp, i64, cdp, i64, cdp, i64, dp, i64]),
         "or_householder": (None, [i64, i64, cdp, i64, dp, i64, dp, i64]),
     }
@@ -228,16 +229,40 @@ def cqr2gs(A, b, check=True):
     return _ret(Q, R, st, check, "cqr2gs")
 
 
-def mcqr2gs(A, b, check=True, literal_r=False, adaptive=False):
+def mcqr2gs(A, b, check=True, literal_r=False, adaptive=False, inplace=False):
     """Alg. 9 (modified CholeskyQR2 with Gram-Schmidt), panel width b.
-    adaptive=True: the runtime choice of the second CholeskyQR pass (Sec. 7)."""
+    adaptive=True: the runtime choice of the second CholeskyQR pass (Sec. 7).
+    inplace=True: A must be a Fortran-ordered float64 array; it is
+    overwritten by Q instead of copied first (for matrices of tens of GB)."""
     lib = _load()
-    A = _f64(A)
+    if inplace:
+        if not (isinstance(A, np.ndarray) and A.dtype == np.float64 and A.flags.f_contiguous):
+            raise ValueError("inplace=True needs a Fortran-ordered float64 array")
+    else:
+        A = _f64(A)
     m, n = A.shape
     R = np.zeros((n, n), order="F")
     flags = (LITERAL_R if literal_r else 0) | (ADAPTIVE if adaptive else 0)
     st = lib.or_mcqr2gs(m, n, int(b), _p(A), max(m, 1), _p(R), n, flags)
     return _ret(A, R, int(st), check, "mcqr2gs")
+
+
+def mcqr2gs_halving(A, b, check=True):
+    """Alg. 9 with the adaptive panel width: a panel whose first CholeskyQR
+    breaks down or has (max U_ii / min U_ii)^2 > 1/(64 u) is retried with the
+    largest divisor of b that is <= b/2, and later panels keep that width.
+    Returns (Q, R, b_final), or (Q, R, b_final, status) with check=False."""
+    lib = _load()
+    A = _f64(A)
+    m, n = A.shape
+    R = np.zeros((n, n), order="F")
+    bf = ctypes.c_int64(0)
+    st = int(lib.or_mcqr2gs_halving(m, n, int(b), _p(A), max(m, 1), _p(R), n, ctypes.byref(bf)))
+    if check:
+        if st != 0:
+            raise OracleError(st, "mcqr2gs_halving")
+        return A, R, int(bf.value)
+    return A, R, int(bf.value), st
 
 
 def _ret(Q, R, st, check, what):

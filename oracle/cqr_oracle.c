@@ -29,6 +29,9 @@
  *   or_cqrgs       Alg. 6 (CholeskyQR with block Gram-Schmidt)
  *   or_cqr2gs      Alg. 7 (CholeskyQR2 with Gram-Schmidt)
  *   or_mcqr2gs     Alg. 9 (modified CholeskyQR2 with Gram-Schmidt)
+ *   or_mcqr2gs_halving  Alg. 9 with the adaptive panel width after a
+ *                  rejected panel (Sec. 5.3-5.4, Eq. cond_bounds; the
+ *                  rule is a reading, see the function)
  *   or_scqr        Alg. 4 (shifted CholeskyQR)
  *   or_scqr3       Alg. 5 (shifted CholeskyQR3)
  *   or_backward    adjoint of A = QR (not in the paper; the standard reverse-
@@ -403,6 +406,95 @@ int or_mcqr2gs(i64 m, i64 n, i64 b, double* X, i64 ldx, double* R, i64 ldr, int 
         for (i64 a = 0; a < jb; ++a) AT(R, ldr, a, jb + c) += ZS[a + c * jb];
     }
   }
+  free(S1);
+  free(S2);
+  free(Z);
+  free(ZS);
+  return st;
+}
+
+/* Adaptive panel width (the paper's remedy for a Cholesky breakdown is a
+ * smaller b, Sec. 5.3-5.4 and Eq. cond_bounds; the rule itself is this
+ * library's reading).  Alg. 9 with panels whose width may shrink: the first
+ * CholeskyQR of every panel (Alg. 9 step 1 for panel 1, step 6 for the
+ * others) forms W = A_j^T A_j and its Cholesky factor U, and the panel is
+ * REJECTED when the factorisation breaks down or when
+ * (max_i U_ii / min_i U_ii)^2 > 1/(64 u), i.e. when the panel's Gram matrix
+ * is within a factor 64 of numerical singularity.  A rejected panel is left
+ * untouched (no triangular solve); b becomes the largest proper divisor of
+ * b that is <= b/2 (so it still divides the remaining width) and the step is
+ * retried on the narrower panel; every later panel keeps the new width.  A
+ * one-column panel is never rejected by the ratio test; its breakdown is
+ * reported as usual.  Projections use the width of the panel they project
+ * on (Alg. 9 step 3 with Q_{j-1} of its own width).  With no rejection this
+ * performs exactly the operations of or_mcqr2gs.  *b_final receives the
+ * width of the last panel.  Returns 0 or the breakdown column + 1. */
+static i64 halved_width(i64 b) {
+  for (i64 d = b / 2; d > 1; --d)
+    if (b % d == 0) return d;
+  return 1;
+}
+
+static int reject_panel(i64 b, const double* U, i64 ldu, int chol_status) {
+  if (b <= 1) return 0;
+  if (chol_status) return 1;
+  double dmax = AT(U, ldu, 0, 0), dmin = AT(U, ldu, 0, 0);
+  for (i64 i = 1; i < b; ++i) {
+    double d = AT(U, ldu, i, i);
+    if (d > dmax) dmax = d;
+    if (d < dmin) dmin = d;
+  }
+  return dmax * dmax * 64.0 * ldexp(1.0, -53) > dmin * dmin;
+}
+
+int or_mcqr2gs_halving(i64 m, i64 n, i64 b, double* X, i64 ldx, double* R, i64 ldr, i64* b_final) {
+  if (b <= 0 || n % b) return -3;
+  zero_mat(n, n, R, ldr);
+  double* W = (double*)malloc(sizeof(double) * (size_t)(b * b));
+  double* S1 = (double*)malloc(sizeof(double) * (size_t)(b * b));
+  double* S2 = (double*)malloc(sizeof(double) * (size_t)(b * b));
+  double* Z = (double*)malloc(sizeof(double) * (size_t)(n * b));
+  double* ZS = (double*)malloc(sizeof(double) * (size_t)(n * b));
+  i64 bw = b, bprev = 0, c0 = 0;
+  int st = 0;
+  while (c0 < n && !st) {
+    double* Aj = X + c0 * ldx;
+    if (c0 > 0) {
+      /* steps 3-5: Y = Q_{j-1}^T A_{j:k}; A_{j:k} -= Q_{j-1} Y; R_{j-1,j:k} = Y */
+      double* Qprev = X + (c0 - bprev) * ldx;
+      double* Yp = &AT(R, ldr, c0 - bprev, c0);
+      or_tn(m, bprev, n - c0, Qprev, ldx, Aj, ldx, Yp, ldr);
+      or_update(m, bprev, n - c0, Aj, ldx, Qprev, ldx, Yp, ldr);
+    }
+    /* step 1 (first pass) / step 6: the first CholeskyQR, with the panel test */
+    for (;;) {
+      or_gram(m, bw, Aj, ldx, W, bw);
+      st = or_chol(bw, W, bw, S1, bw);
+      if (!reject_panel(bw, S1, bw, st)) break;
+      bw = halved_width(bw);
+    }
+    if (st) { st += (int)c0; break; }
+    or_trsm(m, bw, Aj, ldx, S1, bw);
+    if (c0 > 0) {
+      /* step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z */
+      or_tn(m, c0, bw, X, ldx, Aj, ldx, Z, c0);
+      or_update(m, c0, bw, Aj, ldx, X, ldx, Z, c0);
+    }
+    /* step 1 (second pass) / step 8 */
+    st = or_cqr(m, bw, Aj, ldx, S2, bw);
+    if (st) { st += (int)c0; break; }
+    /* R_jj = S2 S1;  R_{1:j-1,j} += Z S1 */
+    small_mm(bw, bw, bw, S2, bw, 1, S1, bw, 1, &AT(R, ldr, c0, c0), ldr);
+    if (c0 > 0) {
+      small_mm(c0, bw, bw, Z, c0, 0, S1, bw, 1, ZS, c0);
+      for (i64 c = 0; c < bw; ++c)
+        for (i64 a = 0; a < c0; ++a) AT(R, ldr, a, c0 + c) += ZS[a + c * c0];
+    }
+    bprev = bw;
+    c0 += bw;
+  }
+  if (b_final) *b_final = bw;
+  free(W);
   free(S1);
   free(S2);
   free(Z);

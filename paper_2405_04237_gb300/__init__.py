@@ -26,7 +26,7 @@ __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
     "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "probe_fp64", "colmajor", "empty_colmajor",
     "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size", "qr_batched", "CQRBatchedFunction",
-    "use_torch_allocator",
+    "use_torch_allocator", "read_panel_width",
 ]
 
 
@@ -112,15 +112,25 @@ def default_panel(n: int) -> int:
     return int(load().cqr_default_panel(int(n)))
 
 
-def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs", emulated: bool = False) -> int:
-    return int(load().cqr_workspace_size(int(m), int(n), int(panel_b),
-                                         _variant(variant) | (_capi.EMULATED if emulated else 0)))
+def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs", emulated: bool = False,
+                   halving: bool = False) -> int:
+    return int(load().cqr_workspace_size(int(m), int(n), int(panel_b), _variant(variant) | (
+        _capi.EMULATED if emulated else 0) | (_capi.HALVE if halving else 0)))
 
 
 def batched_workspace_size(ms, ns, panel_b, variant="mcqr2gs") -> int:
     B = len(ms)
     return int(load().cqr_batched_workspace_size(B, (ctypes.c_int64 * B)(*ms), (ctypes.c_int64 * B)(*ns),
                                                  (ctypes.c_int * B)(*[int(b) for b in panel_b]), _variant(variant)))
+
+
+def read_panel_width(workspace: torch.Tensor, stream=None) -> int:
+    """Width of the last panel of the last halving=True factorisation that used `workspace`."""
+    b = ctypes.c_int(0)
+    rc = load().cqr_read_panel_width(_ptr(workspace), _stream(stream), ctypes.byref(b))
+    if rc != 0:
+        raise CQRError(rc, "cqr_read_panel_width")
+    return int(b.value)
 
 
 def read_status(workspace: torch.Tensor, stream=None) -> int:
@@ -133,7 +143,7 @@ def read_status(workspace: torch.Tensor, stream=None) -> int:
 
 def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: bool = False, check: bool = True,
            out=None, workspace: torch.Tensor | None = None, stream=None, lookahead: bool = False,
-           adaptive: bool = False, emulated: bool = False):
+           adaptive: bool = False, emulated: bool = False, halving: bool = False, info: dict | None = None):
     """A = Q R.  Returns (Q, R) as column-major FP64 tensors.
 
     inplace=True overwrites A's (column-major) storage with Q.  lookahead=True
@@ -141,7 +151,11 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
     stream (bitwise-identical results).  adaptive=True (mCQR2GS) applies the
     runtime choice of the second CholeskyQR pass per panel.  emulated=True
     (mCQR2GS) runs the m-row products (Gram matrices, projections, updates)
-    on the FP8 tensor cores with the FP64-accurate Ozaki splitting.  check=True
+    on the FP8 tensor cores with the FP64-accurate Ozaki splitting.
+    halving=True (mCQR2GS) applies the adaptive panel width: a panel whose
+    first CholeskyQR breaks down or is too ill-conditioned is retried with a
+    halved width (synchronous; the final width goes to info["panel_b"] when
+    a dict is given).  check=True
     synchronises the stream and raises CQRError on a Cholesky breakdown; with
     check=False the call is fully asynchronous (and graph-capturable when a
     workspace and outputs are supplied).
@@ -159,7 +173,7 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
         Q = Ac if inplace else empty_colmajor(m, n, A.device)
         R = empty_colmajor(n, n, A.device)
     flags = var | (_capi.LOOKAHEAD if lookahead else 0) | (_capi.ADAPTIVE if adaptive else 0) | (
-        _capi.EMULATED if emulated else 0)
+        _capi.EMULATED if emulated else 0) | (_capi.HALVE if halving else 0)
     ws_bytes = L.cqr_workspace_size(m, n, int(panel_b), flags)
     if ws_bytes == 0:
         raise CQRError(-5 if n > 0 and m >= n else -1, "cqr_workspace_size")
@@ -172,6 +186,8 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
                       _ptr(workspace), ctypes.c_size_t(workspace.numel()), st)
     if rc != 0:
         raise CQRError(rc, "cqr_factor")
+    if halving and info is not None:
+        info["panel_b"] = read_panel_width(workspace, stream)
     if check:
         s = read_status(workspace, stream)
         if s != 0:

@@ -19,6 +19,7 @@ MCQR2GS, CQR2GS, CQR2, SCQR3 = 0, 1, 2, 3
 LOOKAHEAD = 0x100
 ADAPTIVE = 0x200
 EMULATED = 0x400
+HALVE = 0x800
 VARIANTS = {"mcqr2gs": MCQR2GS, "cqr2gs": CQR2GS, "cqr2": CQR2, "scqr3": SCQR3}
 ERR_CUDA = -1000
 STATUS_TIMEOUT = -2000
@@ -29,7 +30,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTS = [
-    "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status", "cqr_set_allocator",
+    "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status", "cqr_read_panel_width", "cqr_set_allocator",
     "cqr_backward_workspace_size", "cqr_backward", "cqr_batched_workspace_size",
     "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak", "cqr_probe_fp64",
     "cqr_factor_noalloc", "cqr_test_arm_wait_expiry", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
@@ -71,6 +72,7 @@ def load(build_if_missing: bool = True):
             "cqr_default_panel": (c_int, [i64]),
             "cqr_factor": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, sz, vp]),
             "cqr_read_status": (c_int, [vp, vp, PI]),
+            "cqr_read_panel_width": (c_int, [vp, vp, PI]),
             "cqr_set_allocator": (c_int, [ALLOC_FN, FREE_FN, vp]),
             "cqr_factor_noalloc": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, vp]),
             "cqr_backward_workspace_size": (sz, [i64, i64]),

@@ -16,11 +16,22 @@ namespace {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t status, skip, W, S1, S2, rinv, Z, R1, R2, part, oz, total;
+  size_t status, skip, panel, W, S1, S2, rinv, Z, R1, R2, part, oz, total;
 };
 
+// Offsets of the words cqr_read_status and cqr_read_panel_width read.
+constexpr size_t kStatusOffset = 0, kPanelOffset = 512;
+
+// Panel width after a rejected panel (adaptive width): the largest divisor
+// of b that is <= b/2, so that it still divides the remaining width.
+int halved_width(int b) {
+  for (int d = b / 2; d > 1; --d)
+    if (b % d == 0) return d;
+  return 1;
+}
+
 // Workspace plan.  The status word sits at offset 0 (cqr_read_status).
-Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
+Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false, bool halving = false) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -32,6 +43,7 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
   const i64 pw = whole ? n : b;  // panel width of every CQR
   L.status = take(sizeof(int));
   L.skip = take(sizeof(int));
+  L.panel = take(sizeof(int));  // == kPanelOffset: every entry is 256-byte aligned
   L.W = take(sizeof(double) * pw * pw);
   L.S1 = take(sizeof(double) * pw * pw);
   L.S2 = take(sizeof(double) * pw * pw);
@@ -54,6 +66,31 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
       }
     }
   }
+  if (halving && variant == CQR_MCQR2GS) {
+    // every width of the chain b, h(b), h(h(b)), ..., 1 at every position it
+    // can start from (a multiple of itself), after a panel of any wider width
+    int chain[40], nc = 0;
+    for (int w = b;; w = halved_width(w)) {
+      chain[nc++] = w;
+      if (w == 1) break;
+    }
+    for (int i = 0; i < nc; ++i) {
+      const int w2 = chain[i];
+      const size_t g = tn_partial_doubles(m, w2, w2, 1);
+      if (g > pd) pd = g;
+      for (i64 c0 = w2; c0 < n; c0 += w2) {
+        for (int h = 0; h <= i; ++h) {
+          const int w1 = chain[h];
+          if (c0 >= w1 && c0 % w1 == 0) {
+            const size_t d = tn_partial_doubles(m, w1, (int)(n - c0), 0);
+            if (d > pd) pd = d;
+          }
+        }
+        const size_t d = tn_partial_doubles(m, (int)c0, w2, 0);
+        if (d > pd) pd = d;
+      }
+    }
+  }
   L.part = take(sizeof(double) * pd);
   size_t oz = 0;
   if (emulated && variant == CQR_MCQR2GS) {  // Gram matrices; products with Y (b x w) and Z (jb x b) of Alg. 9
@@ -68,12 +105,13 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false) {
   }
   L.oz = take(oz);
   L.total = off;
+  static_assert(kStatusOffset == 0, "status word first");
   return L;
 }
 
 struct Work {
   int* status;
-  int* skip;  // second-pass decision of the runtime repetition choice
+  int* skip;  // second-pass decision of the runtime repetition choice; panel test of the adaptive width
   double *W, *S1, *S2, *rinv, *Z, *R1, *R2, *part;
   void* oz;   // emulated projections and updates (null: native FP64)
 };
@@ -247,6 +285,51 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
   return join_side(st, side, &pending);
 }
 
+// Alg. 9 with the adaptive panel width (CQR_HALVE): the first CholeskyQR of
+// every panel (step 1's first pass, step 6) is tested on the device (the
+// Cholesky kernel's panel test) and the host reads the decision before it
+// enqueues the triangular solve; a rejected panel, left untouched, is
+// retried with halved_width(b), which every later panel keeps.  The same
+// rule as the oracle's or_mcqr2gs_halving; one host synchronisation per
+// attempt.  *b_final receives the last panel's width.
+cudaError_t mcqr2gs_halving_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w,
+                                cudaStream_t st, bool adaptive, int* b_final) {
+  int bw = b, bprev = 0;
+  for (i64 c0 = 0; c0 < n;) {
+    double* Aj = Q + c0 * ldq;
+    if (c0 > 0) {  // steps 3-5 with the previous panel (its own width)
+      const double* Qprev = Q + (c0 - bprev) * ldq;
+      double* Yp = R + (c0 - bprev) + c0 * ldr;
+      TRY(tn_product(m, bprev, (int)(n - c0), Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
+      TRY(nn_product(m, (int)(n - c0), bprev, Qprev, ldq, Yp, ldr, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    }
+    for (;;) {  // the first CholeskyQR's Gram and Cholesky, with the panel test
+      int rej = 0;
+      TRY(cudaMemsetAsync(w.skip, 0, sizeof(int), st));
+      TRY(tn_product(m, bw, bw, Aj, ldq, Aj, ldq, 1, w.part, w.W, bw, w.status, st));
+      TRY(chol_factor(bw, w.W, bw, w.S1, bw, w.rinv, (int)c0, w.status, 0, m, st, nullptr, w.skip));
+      TRY(cudaMemcpyAsync(&rej, w.skip, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TRY(cudaStreamSynchronize(st));
+      if (!rej) break;
+      bw = halved_width(bw);
+    }
+    TRY(trsm_any(m, bw, Aj, ldq, w.S1, bw, w.rinv, w.status, st));
+    if (c0 > 0) {  // step 7
+      TRY(tn_product(m, (int)c0, bw, Q, ldq, Aj, ldq, 0, w.part, w.Z, c0, w.status, st));
+      TRY(nn_product(m, bw, (int)c0, Q, ldq, w.Z, c0, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    }
+    // step 1's second pass / step 8
+    TRY(cqr_panel(m, bw, Aj, ldq, w.S2, bw, w, (int)c0, 0, st, adaptive));
+    // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
+    TRY(nn_product(bw, bw, bw, w.S2, bw, w.S1, bw, R + c0 + c0 * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
+    if (c0 > 0) TRY(nn_product(c0, bw, bw, w.Z, c0, w.S1, bw, R + c0 * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
+    bprev = bw;
+    c0 += bw;
+  }
+  *b_final = bw;
+  return cudaSuccess;
+}
+
 cudaError_t factor_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, int variant, const Work& w,
                        cudaStream_t st, const Side* side = nullptr, bool adaptive = false) {
   switch (variant) {
@@ -370,13 +453,14 @@ static int resolve_panel(int64_t n, int panel_b, int variant) {
 
 size_t cqr_workspace_size(int64_t m, int64_t n, int panel_b, int variant_flags) {
   const bool emulated = (variant_flags & CQR_EMULATED) != 0;
-  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED);
+  const bool halving = (variant_flags & CQR_HALVE) != 0;
+  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED | CQR_HALVE);
   if (m < 1 || n < 1 || m < n || variant < 0 || variant > 3) return 0;
   if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > CQR_MAX_PANEL) return 0;
   const int b = resolve_panel(n, panel_b, variant);
   if (b < 1 || b > CQR_MAX_PANEL || n % b) return 0;
-  if (emulated && variant != CQR_MCQR2GS) return 0;
-  return make_layout(m, n, b, variant, emulated).total;
+  if ((emulated || halving) && variant != CQR_MCQR2GS) return 0;
+  return make_layout(m, n, b, variant, emulated, halving).total;
 }
 
 int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
@@ -384,7 +468,8 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   const bool lookahead = (variant_flags & CQR_LOOKAHEAD) != 0;
   const bool adaptive = (variant_flags & CQR_ADAPTIVE) != 0;
   const bool emulated = (variant_flags & CQR_EMULATED) != 0;
-  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED);
+  const bool halving = (variant_flags & CQR_HALVE) != 0;
+  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED | CQR_HALVE);
   if (m < 1 || m < n) return -1;
   if (n < 1) return -2;
   if (!A) return -3;
@@ -398,8 +483,9 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   if (Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
   if (!R) return -8;
   if (ldr < n) return -9;
-  if ((emulated || adaptive) && variant != CQR_MCQR2GS) return -10;
-  const Layout L = make_layout(m, n, b, variant, emulated);
+  if ((emulated || adaptive || halving) && variant != CQR_MCQR2GS) return -10;
+  if (halving && (emulated || lookahead)) return -10;
+  const Layout L = make_layout(m, n, b, variant, emulated, halving);
   cudaStream_t st = (cudaStream_t)stream;
   if (!workspace) {
     Allocator al;
@@ -418,7 +504,14 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
                                   cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return CQR_ERR_CUDA;
   if (cudaMemset2DAsync(R, sizeof(double) * ldr, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
-  if (lookahead && (variant == CQR_MCQR2GS || variant == CQR_CQR2GS)) {
+  if (halving) {
+    int b_final = b;
+    if (mcqr2gs_halving_run(m, n, b, Q, ldq, R, ldr, w, st, adaptive, &b_final) != cudaSuccess) return CQR_ERR_CUDA;
+    if (cudaMemcpyAsync((char*)workspace + kPanelOffset, &b_final, sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return CQR_ERR_CUDA;
+  } else if (lookahead && (variant == CQR_MCQR2GS || variant == CQR_CQR2GS)) {
     std::lock_guard<std::mutex> lk(g_side_mu);
     const Side* side = get_side();
     if (!side) return CQR_ERR_CUDA;
@@ -426,6 +519,18 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   } else if (factor_run(m, n, b, Q, ldq, R, ldr, variant, w, st, nullptr, adaptive) != cudaSuccess) {
     return CQR_ERR_CUDA;
   }
+  return 0;
+}
+
+int cqr_read_panel_width(const void* workspace, cqr_stream_t stream, int* panel_b) {
+  if (!workspace || !panel_b) return -1;
+  int h = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&h, (const char*)workspace + kPanelOffset, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return CQR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CQR_ERR_CUDA;
+  *panel_b = h;
   return 0;
 }
 

@@ -79,9 +79,12 @@ cudaError_t nn_product_t(i64 M, int N, int K, const double* A, i64 lda, const do
 // shifted-CholeskyQR shift s = sqrt(m) * 2^-53 * trace(W) first (Alg. 4).
 // With `skip` non-null the second-pass rule of the runtime repetition
 // choice applies: if every entry of U - I is within 8u, U := I exactly and
-// *skip = 1 (else 0).
+// *skip = 1 (else 0).  With `reject` non-null the panel test of the adaptive
+// panel width applies: *reject = 1 when b > 1 and the factorisation broke
+// down (status then left untouched) or (max U_jj / min U_jj)^2 > 1/(64 u),
+// else 0.  The kernel returns early, writing nothing, if *status != 0.
 cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* rinv, int col0, int* status,
-                        int shift_fro, i64 m, cudaStream_t st, int* skip = nullptr);
+                        int shift_fro, i64 m, cudaStream_t st, int* skip = nullptr, int* reject = nullptr);
 
 // ---------------------------------------------------------------------------
 // Row-wise forward substitution  X := X U^{-1}  (X m x b, b <= kTrsmMaxB),

@@ -29,7 +29,7 @@ constexpr int kCholThreads = 512;
 template <bool SMEM>
 __global__ void __launch_bounds__(kCholThreads) chol_kernel(int b, double* W, i64 ldw, double* U, i64 ldu,
                                                             double* rinv, int col0, int* status, int shift, i64 m,
-                                                            int* skip) {
+                                                            int* skip, int* reject) {
   extern __shared__ __align__(16) double sm[];
   if (status && *status) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = kCholThreads / 32;
@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(int b, double* W, i6
         }
       } else if (lane == 0) {
         broken = j;
-        if (status) atomicCAS(status, 0, col0 + j + 1);
+        // with the panel test of the adaptive width, a breakdown of a panel wider
+        // than one column is a rejection, not a failure of the factorisation
+        if (status && !(reject && b > 1)) atomicCAS(status, 0, col0 + j + 1);
       }
     }
     __syncthreads();
@@ -97,6 +99,25 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(int b, double* W, i6
     __syncthreads();
   }
   const int jb = broken;
+  // Panel test of the adaptive panel width: rejected when the factorisation
+  // broke down or (max U_jj / min U_jj)^2 > 1/(64 u); one column never is.
+  if (reject && t == 0) {
+    int rej = 0;
+    if (b > 1) {
+      if (jb >= 0) {
+        rej = 1;
+      } else {
+        double dmax = at(0, 0), dmin = at(0, 0);
+        for (int j = 1; j < b; ++j) {
+          const double d = at(j, j);
+          if (d > dmax) dmax = d;
+          if (d < dmin) dmin = d;
+        }
+        rej = dmax * dmax * 64.0 * 0x1p-53 > dmin * dmin;
+      }
+    }
+    *reject = rej;
+  }
   // Runtime choice of the second CholeskyQR pass (Sec. 7): when every entry
   // of U - I is within 8u the panel is already orthonormal to working
   // precision; U becomes I exactly and the triangular solve is skipped
@@ -144,7 +165,7 @@ __global__ void diag_reciprocal_kernel(int n, const double* R, i64 ldr, double* 
 }  // namespace
 
 cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* rinv, int col0, int* status,
-                        int shift_fro, i64 m, cudaStream_t st, int* skip) {
+                        int shift_fro, i64 m, cudaStream_t st, int* skip, int* reject) {
   if (b <= 0) return cudaSuccess;
   if (b <= 128) {
     const size_t smem = sizeof(double) * ((size_t)2 * b + (size_t)b * b);
@@ -155,12 +176,14 @@ cudaError_t chol_factor(int b, double* W, i64 ldw, double* U, i64 ldu, double* r
       attr = true;
     }
     prof_begin(kCholesky, st);
-    chol_kernel<true><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m, skip);
+    chol_kernel<true><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m, skip,
+                                                     reject);
     prof_end(kCholesky, (double)b * b * b / 3.0, st);
   } else {
     const size_t smem = sizeof(double) * (size_t)2 * b;
     prof_begin(kCholesky, st);
-    chol_kernel<false><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m, skip);
+    chol_kernel<false><<<1, kCholThreads, smem, st>>>(b, W, ldw, U, ldu, rinv, col0, status, shift_fro, m, skip,
+                                                      reject);
     prof_end(kCholesky, (double)b * b * b / 3.0, st);
   }
   return cudaGetLastError();

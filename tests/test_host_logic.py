@@ -60,11 +60,29 @@ def test_factor_argument_codes(L):
     assert factor_rc(L, variant=4) == -10                      # unknown variant
     assert factor_rc(L, variant=CG | _capi.EMULATED) == -10    # emulation is mCQR2GS only
     assert factor_rc(L, variant=CG | _capi.ADAPTIVE) == -10    # adaptive repetitions are mCQR2GS only
+    assert factor_rc(L, variant=CG | _capi.HALVE) == -10       # adaptive panel width: mCQR2GS only
+    assert factor_rc(L, variant=MC | _capi.HALVE | _capi.EMULATED) == -10
+    assert factor_rc(L, variant=MC | _capi.HALVE | _capi.LOOKAHEAD) == -10
     assert factor_rc(L, ws=0) == -11                           # workspace null
     assert factor_rc(L, ws=W_ADDR + 8) == -11                  # workspace not 256-byte aligned
     need = L.cqr_workspace_size(1000, 64, 16, MC)
     assert need > 0
     assert factor_rc(L, ws_bytes=need - 1) == -12              # workspace too small
+
+
+def test_halving_workspace_covers_every_width(L):
+    """The adaptive width's workspace holds the partial sums of every width
+    the chain b, b/2, ..., 1 can reach, so it is never smaller than the
+    fixed-width workspace of any width on the chain."""
+    for m, n, b in ((100000, 1024, 128), (20000, 96, 24), (5000, 64, 64)):
+        need = L.cqr_workspace_size(m, n, b, MC | _capi.HALVE)
+        w = b
+        while True:
+            assert need >= L.cqr_workspace_size(m, n, w, MC)
+            if w == 1:
+                break
+            w = max(d for d in range(1, w // 2 + 1) if w % d == 0)
+    assert L.cqr_workspace_size(1000, 64, 16, CG | _capi.HALVE) == 0
 
 
 def test_workspace_sizes(L):

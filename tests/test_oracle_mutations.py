@@ -61,6 +61,13 @@ MUTATIONS = [
      "  if (!st) st = or_cqr(m, n, X, ldx, R2, n);"),
     ("adaptive: threshold too loose", "const double tau = 8.0 * ldexp(1.0, -53);", "const double tau = ldexp(1.0, -20);"),
     ("adaptive: never fires", "const double tau = 8.0 * ldexp(1.0, -53);", "const double tau = 0.0;"),
+    ("halving: breakdown not rejected", "  if (chol_status) return 1;\n", "  if (chol_status) return 0;\n"),
+    ("halving: bound without the factor 64", "return dmax * dmax * 64.0 * ldexp(1.0, -53) > dmin * dmin;",
+     "return dmax * dmax * ldexp(1.0, -53) > dmin * dmin;"),
+    ("halving: bound 16x tighter", "return dmax * dmax * 64.0 * ldexp(1.0, -53) > dmin * dmin;",
+     "return dmax * dmax * 1024.0 * ldexp(1.0, -53) > dmin * dmin;"),
+    ("halving: Z S1 term dropped", "        for (i64 a = 0; a < c0; ++a) AT(R, ldr, a, c0 + c) += ZS[a + c * c0];",
+     "        for (i64 a = 0; a < c0; ++a) AT(R, ldr, a, c0 + c) += 0.0 * ZS[a + c * c0];"),
 ]
 
 
@@ -157,6 +164,26 @@ def _pins(o) -> dict:
         return rel_diff(o.backward(Q, R, dQ, dR), At.grad.numpy()) < 1e-10
 
     check("adjoint", adjoint)
+
+    def halving():
+        # no rejection: Alg. 9 itself (ratio at 0.35 of the bound)
+        X = make_test_matrix(2000, 40, 1e15, seed=1)
+        Q, R, bf = o.mcqr2gs_halving(X, 20)
+        Q0, R0 = o.mcqr2gs(X, 20)
+        ok = bf == 20 and np.array_equal(Q, Q0) and np.array_equal(R, R0)
+        # first panel rejected by the ratio alone (10x over the bound): Alg. 9 with b = 10
+        X = make_test_matrix(2000, 40, 1e15, seed=8)
+        Q, R, bf = o.mcqr2gs_halving(X, 20)
+        Q0, R0 = o.mcqr2gs(X, 10)
+        ok = ok and bf == 10 and np.array_equal(Q, Q0) and np.array_equal(R, R0)
+        # two-panel breakdowns recovered to O(u)
+        for m, n, seed in ((2000, 40, 2), (4000, 80, 6)):
+            X = make_test_matrix(m, n, 1e15, seed)
+            Q, R, bf, st = o.mcqr2gs_halving(X, n // 2, check=False)
+            ok = ok and st == 0 and bf < n // 2 and orth_err(Q) < 1e-13 and resid(X, Q, R) < 1e-14
+        return ok
+
+    check("halving", halving)
     return res
 
 

@@ -10,7 +10,12 @@ Each test fixes the oracle with an independent fact:
   * the paper's stability claims (Sec. 4, 5.3, 5.4) on scaled-down matrices,
   * a planted mistake (the paper-literal R of Alg. 9, which omits the
     re-orthogonalisation coefficients) must be caught by the residual pin,
-  * finite differences and torch.linalg.qr for the adjoint.
+  * finite differences and torch.linalg.qr for the adjoint,
+  * the adaptive panel width (or_mcqr2gs_halving) against the pinned
+    or_mcqr2gs: identical when no panel is rejected, identical to the
+    narrower width when the first panel is, decisions equal to the rule
+    evaluated independently (LAPACK Cholesky of numpy's Gram matrix), and
+    the paper's O(u) accuracy where plain two-panel mCQR2GS breaks down.
 """
 import numpy as np
 import pytest
@@ -365,3 +370,74 @@ def test_sigma_recipe():
     A = make_test_matrix(300, 10, 1e6, seed=1)
     sv = np.linalg.svd(A, compute_uv=False)
     assert abs(sv[0] / sv[-1] / 1e6 - 1) < 1e-6
+
+
+# --------------------------------------------------------------------------- adaptive panel width
+U_RULE = 1.0 / (64.0 * 2.0 ** -53)  # panel rejected when (max U_ii / min U_ii)^2 exceeds this
+
+
+def independent_reject(X):
+    """The panel test evaluated outside the oracle: LAPACK Cholesky of numpy's
+    Gram matrix; a breakdown (not positive definite) rejects too."""
+    try:
+        L = np.linalg.cholesky(X.T @ X)
+    except np.linalg.LinAlgError:
+        return True
+    d = np.diag(L)
+    return (d.max() / d.min()) ** 2 > U_RULE
+
+
+@pytest.mark.parametrize("m,n,b,kappa,seed", [(2000, 40, 20, 1e3, 21), (3000, 60, 20, 1e6, 22),
+                                               (2000, 40, 20, 1e15, 1), (4000, 80, 40, 1e15, 2)])
+def test_halving_without_rejection_is_mcqr2gs(oracle, m, n, b, kappa, seed):
+    """No panel rejected: exactly Alg. 9 with the given width."""
+    A = make_test_matrix(m, n, kappa, seed)
+    assert not independent_reject(A[:, :b])
+    Q, R, bf = oracle.mcqr2gs_halving(A, b)
+    Q0, R0 = oracle.mcqr2gs(A, b)
+    assert bf == b and np.array_equal(Q, Q0) and np.array_equal(R, R0)
+
+
+@pytest.mark.parametrize("seed,why", [(3, "breakdown"), (8, "ratio")])
+def test_halving_at_the_first_panel_is_the_narrower_width(oracle, seed, why):
+    """The first panel rejected (seed 3: its Cholesky breaks down; seed 8: no
+    breakdown, but the diagonal ratio is ~10x over the bound) and nothing
+    later: exactly Alg. 9 with b = 10 from the start."""
+    A = make_test_matrix(2000, 40, 1e15, seed)
+    _, st = oracle.chol(oracle.gram(A[:, :20]))
+    assert (st != 0) == (why == "breakdown")
+    if why == "ratio":  # far from the bound: the same decision outside the oracle
+        assert independent_reject(A[:, :20])
+    Q, R, bf = oracle.mcqr2gs_halving(A, 20)
+    Q0, R0 = oracle.mcqr2gs(A, 10)
+    assert bf == 10 and np.array_equal(Q, Q0) and np.array_equal(R, R0)
+
+
+@pytest.mark.parametrize("m,n,seed", [(2000, 40, 2), (2000, 40, 6), (4000, 80, 6), (4000, 80, 9), (6000, 120, 2)])
+def test_halving_recovers_where_two_panels_break_down(oracle, m, n, seed):
+    """Sec. 5.4: with two panels mCQR2GS can break down at kappa = 1e15; the
+    smaller panel width is the paper's remedy.  Plain Alg. 9 reports a
+    breakdown; the adaptive width finishes with O(u) orthogonality and
+    residual, an upper triangular R with positive diagonal, and the panels
+    before the rejected one untouched."""
+    A = make_test_matrix(m, n, 1e15, seed)
+    b = n // 2
+    Qp, Rp, stp = oracle.mcqr2gs(A, b, check=False)
+    assert stp > 0
+    Q, R, bf = oracle.mcqr2gs_halving(A, b)
+    assert bf < b and n % bf == 0
+    assert orth_err(Q) < 1e-13 and resid(A, Q, R) < 1e-14
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    U1, st1 = oracle.chol(oracle.gram(A[:, :b]))  # the rule on panel 1, from the oracle's own factor
+    d = np.diag(U1)
+    if st1 == 0 and (d.max() / d.min()) ** 2 <= U_RULE:  # rejected at panel 2: panel 1 is plain Alg. 9's
+        assert np.array_equal(Q[:, :b], Qp[:, :b]) and np.array_equal(R[:b, :b], Rp[:b, :b])
+
+
+def test_halving_one_column_breakdown_is_reported(oracle):
+    """A zero column can be cut down to a one-column panel but not further:
+    the breakdown is reported with its global column."""
+    A = make_test_matrix(1000, 8, 1e2, seed=23)
+    A[:, 5] = 0.0
+    _, _, bf, st = oracle.mcqr2gs_halving(A, 8, check=False)
+    assert st == 6 and bf == 1
