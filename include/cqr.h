@@ -268,11 +268,40 @@ int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const doubl
  */
 size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant);
 
+/* Flags OR-ed into `variant` of cqr_factor_batched and
+ * cqr_batched_workspace_size.  CQR_BATCH_POOL forces the stream-pool
+ * schedule; CQR_BATCH_GROUP(G) sets the CTAs per matrix of the persistent
+ * launch (G must divide the SM count; 0 = default, the largest divisor
+ * <= 8); CQR_HALVE (persistent path only) applies the adaptive panel width
+ * on the device. */
+#define CQR_BATCH_POOL 0x1000
+#define CQR_BATCH_GROUP(G) ((G) << 16)
+
 /*
  * cqr_factor_batched: factors `batch` independent matrices A_i = Q_i R_i
  * (variant CQR_MCQR2GS or CQR_CQR2GS).  Not in the paper (batching of many
- * small problems); each matrix follows Alg. 9 / Alg. 7 exactly as
- * cqr_factor() does.
+ * small problems); each matrix follows Alg. 9 / Alg. 7 as cqr_factor()
+ * does.  Two schedules:
+ *   persistent (mCQR2GS, every n_i <= 128, n_i and b_i multiples of 4,
+ *   unless CQR_BATCH_POOL): ONE cooperative kernel launch with one CTA per
+ *   SM.  Groups of G CTAs take whole matrices (a static largest-first
+ *   schedule); the G CTAs of a group split the matrix's rows (the row-block
+ *   distribution of Alg. 2 / Alg. 8), write partial sums of every m-row
+ *   product to their own slots, meet at a group barrier and add the slots
+ *   in rank order, each factoring the b x b Gram matrix redundantly (the
+ *   redundant Cholesky of Alg. 2).  Each pass over a sub-block of rows
+ *   fuses a streaming step with the next m-row product (update + Gram,
+ *   solve + projection, re-orthogonalisation + Gram).  Results match the
+ *   single-matrix path to rounding (a different summation order), not
+ *   bitwise.  Every group-barrier wait is bounded (2 s); on expiry the
+ *   unfinished matrices get CQR_STATUS_TIMEOUT.  With CQR_HALVE a rejected
+ *   panel (see CQR_HALVE) is retried at half width on the device; read the
+ *   final widths with cqr_batched_panel_widths().
+ *   stream pool (CQR2GS, wider matrices, or CQR_BATCH_POOL): each matrix
+ *   runs exactly the kernel sequence of a cqr_factor() call with the same
+ *   sizes and panel width (so its result is bitwise that call's), the
+ *   matrices spread over library-owned streams forked from and joined back
+ *   into `stream`.
  *   batch                  number of matrices, >= 0                  (arg 1)
  *   m, n, lda, panel_b     HOST arrays of length batch                (args 2-5)
  *   A, Q, R                HOST arrays of DEVICE pointers; ldq_i = lda_i
@@ -286,14 +315,10 @@ size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n,
  * The host size arrays come first and the device-pointer arrays after
  * them; Q_i and R_i take the leading dimensions lda_i and n_i, so there are
  * no ldq / ldr arrays.
- * The matrices are distributed (largest work first) over a pool of
- * library-owned streams that are forked from `stream` and joined back into
- * it with events, so small grids, Cholesky islands and reductions of
- * different matrices overlap; the whole call is ordered on `stream`, reads
- * no host memory after it returns, and can be captured into a CUDA graph.
- * Each matrix's result is bitwise identical to a cqr_factor() call with the
- * same sizes and panel width.  Calls that share the workspace must not
- * overlap on the GPU.
+ * Either way the whole call is ordered on `stream`, reads no host memory
+ * after it returns (the persistent path's descriptor table travels as
+ * kernel parameters), and can be captured into a CUDA graph.  Calls that
+ * share the workspace must not overlap on the GPU.
  */
 int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* lda, const int* panel_b,
                        double* const* A, double* const* Q, double* const* R, int variant, int* status,
@@ -315,6 +340,26 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
  * Host-side only (nothing is launched).  Returns 0, or -i for argument i.
  */
 int cqr_test_arm_wait_expiry(int kernel, int stage, long long wait_ns);
+
+/*
+ * cqr_batched_panel_widths: after a persistent cqr_factor_batched call
+ * (synchronises `stream`), copies each matrix's final panel width (its
+ * last panel's, which CQR_HALVE may have narrowed) into the HOST array
+ * panel_b[batch].  Returns 0, -1 (batch < 1), -2 (NULL workspace),
+ * -4 (NULL panel_b) or CQR_ERR_CUDA.
+ */
+int cqr_batched_panel_widths(int batch, const void* workspace, cqr_stream_t stream, int* panel_b);
+
+/*
+ * cqr_test_arm_barrier_expiry: test hook of the persistent batched launch's
+ * bounded group barriers (failure detection; not in the paper).  In the
+ * NEXT persistent launch, CTA `rank` of group `group` skips its arrival at
+ * its `barrier`-th group barrier (1-based) and every barrier wait of that
+ * launch is bounded by `wait_ns`, so the other CTAs' waits expire; the
+ * hook then disarms itself.  group = -1 disarms.  Host-side only.  Returns
+ * 0, or -i for argument i.
+ */
+int cqr_test_arm_barrier_expiry(int group, int rank, int barrier, long long wait_ns);
 
 /* cqr_status_string: static description of a status or return code. */
 const char* cqr_status_string(int status);

@@ -26,7 +26,7 @@ __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
     "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "probe_fp64", "colmajor", "empty_colmajor",
     "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size", "qr_batched", "CQRBatchedFunction",
-    "use_torch_allocator", "read_panel_width",
+    "use_torch_allocator", "read_panel_width", "batched_panel_widths",
 ]
 
 
@@ -118,10 +118,27 @@ def workspace_size(m: int, n: int, panel_b: int = 0, variant="mcqr2gs", emulated
         _capi.EMULATED if emulated else 0) | (_capi.HALVE if halving else 0)))
 
 
-def batched_workspace_size(ms, ns, panel_b, variant="mcqr2gs") -> int:
+def _batch_flags(variant, schedule="auto", group=0, halving=False) -> int:
+    if schedule not in ("auto", "pool"):
+        raise ValueError("schedule must be 'auto' (persistent launch where eligible) or 'pool'")
+    return (_variant(variant) | (_capi.BATCH_POOL if schedule == "pool" else 0) | _capi.BATCH_GROUP(group)
+            | (_capi.HALVE if halving else 0))
+
+
+def batched_workspace_size(ms, ns, panel_b, variant="mcqr2gs", schedule="auto", group=0, halving=False) -> int:
     B = len(ms)
     return int(load().cqr_batched_workspace_size(B, (ctypes.c_int64 * B)(*ms), (ctypes.c_int64 * B)(*ns),
-                                                 (ctypes.c_int * B)(*[int(b) for b in panel_b]), _variant(variant)))
+                                                 (ctypes.c_int * B)(*[int(b) for b in panel_b]),
+                                                 _batch_flags(variant, schedule, group, halving)))
+
+
+def batched_panel_widths(workspace: torch.Tensor, batch: int, stream=None) -> list:
+    """Final panel width of each matrix of the last persistent batched call that used `workspace`."""
+    out = (ctypes.c_int * int(batch))()
+    rc = load().cqr_batched_panel_widths(int(batch), _ptr(workspace), _stream(stream), out)
+    if rc != 0:
+        raise CQRError(rc, "cqr_batched_panel_widths")
+    return list(out)
 
 
 def read_panel_width(workspace: torch.Tensor, stream=None) -> int:
@@ -242,10 +259,16 @@ def qr(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs"):
 
 
 def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, stream=None, workspace=None,
-                   status=None, inplace: bool = False):
+                   status=None, inplace: bool = False, schedule: str = "auto", group: int = 0,
+                   halving: bool = False):
     """Factor a list of column-major FP64 CUDA matrices in one batched call.
 
-    Returns a list of (Q_i, R_i).  Each result equals factor(A_i, b_i).
+    Returns a list of (Q_i, R_i).  schedule="auto" runs mCQR2GS batches of
+    matrices with n <= 128 (n, b multiples of 4) as one persistent launch
+    (groups of `group` CTAs per matrix, 0 = library default; halving=True
+    narrows rejected panels on the device) -- equal to factor(A_i, b_i) to
+    rounding; otherwise, or with schedule="pool", each result is bitwise
+    factor(A_i, b_i).
     """
     L = load()
     B = len(As)
@@ -275,14 +298,15 @@ def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, s
     Ap = (ctypes.c_void_p * B)(*[A.data_ptr() for A in Acs])
     Qp = (ctypes.c_void_p * B)(*[Q.data_ptr() for Q in Qs])
     Rp = (ctypes.c_void_p * B)(*[R.data_ptr() for R in Rs])
-    ws_bytes = L.cqr_batched_workspace_size(B, ms, ns, bs, var)
+    flags = _batch_flags(var, schedule, group, halving)
+    ws_bytes = L.cqr_batched_workspace_size(B, ms, ns, bs, flags)
     if ws_bytes == 0:
         raise CQRError(-2, "cqr_batched_workspace_size")
     if workspace is None:
         workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     if status is None:
         status = torch.zeros(B, dtype=torch.int32, device=dev)
-    rc = L.cqr_factor_batched(B, ms, ns, lds, bs, Ap, Qp, Rp, var, _ptr(status), _ptr(workspace),
+    rc = L.cqr_factor_batched(B, ms, ns, lds, bs, Ap, Qp, Rp, flags, _ptr(status), _ptr(workspace),
                               ctypes.c_size_t(workspace.numel()), _stream(stream))
     if rc != 0:
         raise CQRError(rc, "cqr_factor_batched")
@@ -296,9 +320,9 @@ def factor_batched(As, panel_b=None, variant="mcqr2gs", *, check: bool = True, s
 
 class CQRBatchedFunction(torch.autograd.Function):
     """Differentiable A_i -> (Q_i, R_i) for a list of matrices: one batched
-    forward call (cqr_factor_batched), one adjoint call (cqr_backward) per
-    matrix in the backward pass.  Saves only the outputs.  Each Q_i, R_i and
-    each gradient is bitwise the one of a single qr(A_i, b_i) call."""
+    forward call (cqr_factor_batched, persistent launch where eligible), one
+    adjoint call (cqr_backward) per matrix in the backward pass.  Saves only
+    the outputs; each gradient is bitwise backward(Q_i, R_i, Qbar_i, Rbar_i)."""
 
     @staticmethod
     def forward(ctx, panel_b, variant, *As):
@@ -336,20 +360,22 @@ class BatchedGraph:
     (eager) call checks every status; capture happens after it.
     """
 
-    def __init__(self, As, panel_b=None, variant="mcqr2gs"):
+    def __init__(self, As, panel_b=None, variant="mcqr2gs", schedule="auto", group=0, halving=False):
         self.As = [colmajor(A) for A in As]
         self.panel_b = panel_b
         self.variant = variant
+        self.flags = _batch_flags(variant, schedule, group, halving)
         dev = self.As[0].device
         L = load()
         B = len(self.As)
         bs = self._panels()
         ms = (ctypes.c_int64 * B)(*[A.shape[0] for A in self.As])
         ns = (ctypes.c_int64 * B)(*[A.shape[1] for A in self.As])
-        self.workspace = torch.empty(batched_workspace_size(list(ms), list(ns), list(bs), variant),
-                                     dtype=torch.uint8, device=dev)
+        self.workspace = torch.empty(batched_workspace_size(list(ms), list(ns), list(bs), variant, schedule, group,
+                                                            halving), dtype=torch.uint8, device=dev)
         self.status = torch.zeros(B, dtype=torch.int32, device=dev)
-        self.out = factor_batched(self.As, list(bs), variant, workspace=self.workspace, status=self.status)
+        self.out = factor_batched(self.As, list(bs), variant, workspace=self.workspace, status=self.status,
+                                  schedule=schedule, group=group, halving=halving)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
@@ -371,7 +397,7 @@ class BatchedGraph:
         Ap = (ctypes.c_void_p * B)(*[A.data_ptr() for A in self.As])
         Qp = (ctypes.c_void_p * B)(*[Q.data_ptr() for Q, _ in self.out])
         Rp = (ctypes.c_void_p * B)(*[R.data_ptr() for _, R in self.out])
-        rc = L.cqr_factor_batched(B, ms, ns, lds, self._panels(), Ap, Qp, Rp, _variant(self.variant),
+        rc = L.cqr_factor_batched(B, ms, ns, lds, self._panels(), Ap, Qp, Rp, self.flags,
                                   _ptr(self.status), _ptr(self.workspace), ctypes.c_size_t(self.workspace.numel()),
                                   _stream(None))
         if rc != 0:

@@ -20,6 +20,11 @@ LOOKAHEAD = 0x100
 ADAPTIVE = 0x200
 EMULATED = 0x400
 HALVE = 0x800
+BATCH_POOL = 0x1000
+
+
+def BATCH_GROUP(G: int) -> int:
+    return int(G) << 16
 VARIANTS = {"mcqr2gs": MCQR2GS, "cqr2gs": CQR2GS, "cqr2": CQR2, "scqr3": SCQR3}
 ERR_CUDA = -1000
 STATUS_TIMEOUT = -2000
@@ -33,7 +38,7 @@ EXPORTS = [
     "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status", "cqr_read_panel_width", "cqr_set_allocator",
     "cqr_backward_workspace_size", "cqr_backward", "cqr_batched_workspace_size",
     "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak", "cqr_probe_fp64",
-    "cqr_factor_noalloc", "cqr_test_arm_wait_expiry", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
+    "cqr_factor_noalloc", "cqr_test_arm_wait_expiry", "cqr_test_arm_barrier_expiry", "cqr_batched_panel_widths", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
 ]
 KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "misc",
                   "batched"]
@@ -84,6 +89,8 @@ def load(build_if_missing: bool = True):
             "cqr_probe_fp64": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
             "cqr_test_arm_wait_expiry": (c_int, [c_int, c_int, ctypes.c_longlong]),
+            "cqr_test_arm_barrier_expiry": (c_int, [c_int, c_int, c_int, ctypes.c_longlong]),
+            "cqr_batched_panel_widths": (c_int, [c_int, vp, vp, PI]),
             "cqr_launch_count": (ctypes.c_ulonglong, []),
             "cqr_profile_enable": (c_int, [c_int]),
             "cqr_profile_disable": (c_int, []),

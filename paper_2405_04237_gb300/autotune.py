@@ -12,6 +12,14 @@ stability; otherwise b only moves time between kernels, since mCQR2GS costs
      min(m, 2^20) rows, and returns the fastest.
 Results are cached per (GPU name, n, variant, m bucket) in a JSON file next
 to the built library.
+
+autotune_batched() tunes the persistent batched launch the same way, on the
+caller's own batch: the CTAs per matrix G (the launch's tile shape: how many
+SMs split one matrix's rows) and the starting panel count (every matrix
+starts with b_i = n_i / k0), each candidate timed with the adaptive panel
+width switched on -- a panel that is too ill-conditioned is narrowed on the
+device (Sec. 5.3-5.4) -- so no condition-number estimate is needed.  The
+fastest candidate whose every status is 0 wins.
 """
 from __future__ import annotations
 
@@ -103,3 +111,68 @@ def autotune(m: int, n: int, variant: str = "mcqr2gs", kappa: float | None = Non
         cache[key] = {"b": bbest, "ms": times, "m_probe": mp}
         _save_cache(cache)
     return bbest
+
+
+def _batch_key(As, variant):
+    ns = sorted({int(A.shape[1]) for A in As})
+    hist = ",".join(f"{n}:{sum(1 for A in As if A.shape[1] == n)}:{int(math.log2(max(2, sum(A.shape[0] for A in As if A.shape[1] == n))))}"
+                    for n in ns)
+    return f"{torch.cuda.get_device_name()}|batched|{variant}|{len(As)}|{hist}"
+
+
+def starting_panels(ns, k0):
+    """b_i = n_i / k0 where that is a multiple of 4 dividing n_i, else the
+    nearest such width below it (at least 4, at most n_i)."""
+    out = []
+    for n in ns:
+        b = max(4, n // k0)
+        while b > 4 and (n % b or b % 4):
+            b -= 1
+        out.append(min(b, n))
+    return out
+
+
+def autotune_batched(As, variant: str = "mcqr2gs", groups=(4, 8, 19), panel_counts=(1, 2, 4), reps: int = 2,
+                     use_cache: bool = True, verbose: bool = False):
+    """(G, panel_b list) for the persistent batched launch of these matrices."""
+    from . import batched_workspace_size, factor_batched
+
+    ns = [int(A.shape[1]) for A in As]
+    ms = [int(A.shape[0]) for A in As]
+    key = _batch_key(As, variant)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return int(cache[key]["G"]), starting_panels(ns, int(cache[key]["k0"]))
+    best, times = None, {}
+    for k0 in panel_counts:
+        bs = starting_panels(ns, k0)
+        for G in groups:
+            ws = torch.empty(batched_workspace_size(ms, ns, bs, variant, group=G, halving=True), dtype=torch.uint8,
+                             device="cuda")
+            st = torch.zeros(len(As), dtype=torch.int32, device="cuda")
+            factor_batched(As, bs, variant, workspace=ws, status=st, group=G, halving=True, check=False)
+            torch.cuda.synchronize()
+            if int((st != 0).sum()) != 0:
+                continue
+            t = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                factor_batched(As, bs, variant, workspace=ws, status=st, group=G, halving=True, check=False)
+                e1.record()
+                e1.synchronize()
+                t = min(t, e0.elapsed_time(e1))
+            times[f"k0={k0},G={G}"] = t
+            if verbose:
+                print(f"autotune batched k0={k0} G={G}: {t:.2f} ms", flush=True)
+            if best is None or t < best[0]:
+                best = (t, G, k0)
+            del ws
+    if best is None:
+        raise RuntimeError("autotune_batched: no candidate factored every matrix")
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = {"G": best[1], "k0": best[2], "ms": times}
+        _save_cache(cache)
+    return best[1], starting_panels(ns, best[2])

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "cqr.h"
 #include "cqr_common.cuh"
@@ -534,6 +535,14 @@ int cqr_read_panel_width(const void* workspace, cqr_stream_t stream, int* panel_
   return 0;
 }
 
+int cqr_batched_panel_widths(int batch, const void* workspace, cqr_stream_t stream, int* panel_b) {
+  if (batch < 1) return -1;
+  if (!workspace) return -2;
+  if (!panel_b) return -4;
+  return batched_persistent_panels(batch, workspace, panel_b, (cudaStream_t)stream) == cudaSuccess ? 0
+                                                                                                  : CQR_ERR_CUDA;
+}
+
 int cqr_read_status(const void* workspace, cqr_stream_t stream, int* status) {
   if (!workspace || !status) return -1;
   int h = 0;
@@ -676,10 +685,46 @@ size_t batched_slice(int batch, const int64_t* m, const int64_t* n, const int* p
 
 }  // namespace
 
-size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int variant) {
-  if (batch < 0 || (variant != CQR_MCQR2GS && variant != CQR_CQR2GS)) return 0;
+namespace {
+
+// Batched variant word: base variant | CQR_HALVE | CQR_BATCH_POOL | CQR_BATCH_GROUP(G).
+struct BatchMode {
+  int variant, G;
+  bool halve, pool_forced;
+};
+BatchMode batch_mode(int flags) {
+  BatchMode b;
+  b.variant = flags & 0xFF;
+  b.halve = (flags & CQR_HALVE) != 0;
+  b.pool_forced = (flags & CQR_BATCH_POOL) != 0;
+  b.G = (flags >> 16) & 0xFF;
+  return b;
+}
+bool batch_flags_ok(int flags) {
+  return (flags & ~(0xFF | CQR_HALVE | CQR_BATCH_POOL | 0xFF0000)) == 0;
+}
+
+// The persistent path takes mCQR2GS batches of matrices with n <= 128 and
+// n, b multiples of 4, unless the stream pool is forced.
+bool use_persistent(int batch, const int64_t* m, const int64_t* n, const int* panel_b, const BatchMode& md) {
+  if (md.variant != CQR_MCQR2GS || md.pool_forced) return false;
+  std::vector<int> b((size_t)batch);
+  for (int i = 0; i < batch; ++i) b[i] = resolve_panel(n[i], panel_b[i], md.variant);
+  return batched_persistent_eligible(batch, m, n, b.data());
+}
+
+}  // namespace
+
+size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, const int* panel_b, int flags) {
+  const BatchMode md = batch_mode(flags);
+  if (!batch_flags_ok(flags) || batch < 0 || (md.variant != CQR_MCQR2GS && md.variant != CQR_CQR2GS)) return 0;
   if (batch == 0) return 256;
   if (!m || !n || !panel_b) return 0;
+  const int variant = md.variant;
+  for (int i = 0; i < batch; ++i)
+    if (cqr_workspace_size(m[i], n[i], panel_b[i], variant) == 0) return 0;
+  if (use_persistent(batch, m, n, panel_b, md)) return batched_persistent_workspace(batch);
+  if (md.halve) return 0;  // the adaptive width of a batch runs on the persistent path only
   const size_t slice = batched_slice(batch, m, n, panel_b, variant);
   if (slice == 0) return 0;
   const int ns = batch < kBatchStreams ? batch : kBatchStreams;
@@ -687,13 +732,15 @@ size_t cqr_batched_workspace_size(int batch, const int64_t* m, const int64_t* n,
 }
 
 int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int64_t* lda, const int* panel_b,
-                       double* const* A, double* const* Q, double* const* R, int variant, int* status,
+                       double* const* A, double* const* Q, double* const* R, int flags, int* status,
                        void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+  const BatchMode md = batch_mode(flags);
+  const int variant = md.variant;
   if (batch < 0) return -1;
   if (batch == 0) return 0;
   if (!m || !n || !lda || !panel_b) return -2;
   if (!A || !Q || !R) return -6;
-  if (variant != CQR_MCQR2GS && variant != CQR_CQR2GS) return -9;
+  if (!batch_flags_ok(flags) || (variant != CQR_MCQR2GS && variant != CQR_CQR2GS)) return -9;
   if (!status) return -10;
   for (int i = 0; i < batch; ++i) {
     if (m[i] < 1 || n[i] < 1 || m[i] < n[i] || lda[i] < m[i]) return -2;
@@ -702,16 +749,33 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
     if (!A[i] || !Q[i] || !R[i]) return -6;
     if (Q[i] != A[i] && overlaps(A[i], lda[i], m[i], n[i], Q[i], lda[i])) return -7;
   }
+  const bool persistent = use_persistent(batch, m, n, panel_b, md);
+  if (md.halve && !persistent) return -9;
   if (!workspace) {
     Allocator al;
     if (!registered_allocator(&al)) return -11;
-    const size_t need = cqr_batched_workspace_size(batch, m, n, panel_b, variant);
+    const size_t need = cqr_batched_workspace_size(batch, m, n, panel_b, flags);
     return with_allocated_workspace(al, need, (cudaStream_t)stream, false, [&](void* ws) {
-      return cqr_factor_batched(batch, m, n, lda, panel_b, A, Q, R, variant, status, ws, need, stream);
+      return cqr_factor_batched(batch, m, n, lda, panel_b, A, Q, R, flags, status, ws, need, stream);
     });
   }
   if ((uintptr_t)workspace & 255) return -11;
-  if (ws_bytes < cqr_batched_workspace_size(batch, m, n, panel_b, variant)) return -12;
+  if (ws_bytes < cqr_batched_workspace_size(batch, m, n, panel_b, flags)) return -12;
+  if (persistent) {
+    const int grid = batched_persistent_grid();
+    int G = md.G;
+    if (G == 0)  // default: the largest divisor of the grid that is <= 8
+      for (G = 8; grid % G; --G) {
+      }
+    if (grid % G) return -9;
+    std::vector<int> b((size_t)batch);
+    for (int i = 0; i < batch; ++i) b[i] = resolve_panel(n[i], panel_b[i], variant);
+    cudaGetLastError();
+    return batched_persistent_run(batch, m, n, lda, b.data(), A, Q, R, status, workspace, G, md.halve,
+                                  (cudaStream_t)stream) == cudaSuccess
+               ? 0
+               : CQR_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lk(g_pool_mu);
   StreamPool* pool = get_pool();
   if (!pool) return CQR_ERR_CUDA;

@@ -115,6 +115,18 @@ cudaError_t diag_reciprocal(int n, const double* R, i64 ldr, double* rinv, cudaS
 int probe_fp64(int kind, int iters, double* gflops, double* flop_per_clk_sm, double* sm_mhz);
 
 // ---------------------------------------------------------------------------
+// Persistent batched mCQR2GS (k_batched.cu): one cooperative launch over all
+// SMs, groups of G CTAs factoring whole matrices (n <= 128, n and b
+// multiples of 4).  `halve` applies the adaptive panel width on the device.
+bool batched_persistent_eligible(int batch, const int64_t* m, const int64_t* n, const int* b);
+size_t batched_persistent_workspace(int batch);
+int batched_persistent_grid();  // CTAs of the launch: one per SM
+cudaError_t batched_persistent_run(int batch, const int64_t* m, const int64_t* n, const int64_t* lda,
+                                   const int* b, double* const* A, double* const* Q, double* const* R,
+                                   int* status, void* workspace, int G, bool halve, cudaStream_t st);
+cudaError_t batched_persistent_panels(int batch, const void* workspace, int* host_b, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // Launch accounting (prof.cu).  Every launch is wrapped in prof_begin /
 // prof_end with its kernel class and algorithmic FLOP count.
 enum KernelClass {

@@ -20,7 +20,7 @@ namespace cqr {
 namespace {
 
 constexpr int kTnThreads = 256;
-constexpr int kSyrkMaxThreads = 544;  // 17 warps
+constexpr int kSyrkThreads = 512;  // 16 warps
 // Persistent blocks per SM for the split-m grids (at most what the
 // registers allow).  Each block stalls in the load burst at the start of a
 // row block; with three resident blocks the others keep the FP64 pipe busy
@@ -48,35 +48,65 @@ __host__ __device__ inline i64 owner_of(i64 i, i64 T, i64 P) { return ((i + 1) *
 __device__ inline double2 lds2(const double* p) { return *reinterpret_cast<const double2*>(p); }
 
 // ---------------------------------------------------------------------------
-// Gram (syrk) kernel for b <= 128.  One block covers the whole upper
-// triangle: thread t < G*cnt owns upper micro-tile (t % cnt) in group
-// (t / cnt); groups split the rows of each row block.
+// Gram (syrk) kernel for b <= 128, 512 threads (16 warps: four per warp
+// scheduler, so every scheduler's share of the FP64 pipe gets the same
+// work).  The upper triangle is cut into cnt = T(T+1)/2 tiles of 4 x 4
+// (T = ceil(b/4)).  The largest power of two M <= cnt of them are "main"
+// tiles: thread t owns main tile t % M on the rows r = t / M (mod 512 / M)
+// of each staged row block.  The E = cnt - M other tiles are "extra": each
+// is owned by 512 / E threads (whole warps when E <= 16) that split the
+// rows round-robin.  Every thread thus carries one main and at most one
+// extra accumulator and runs the same instruction stream as its warp.
 struct SyrkArgs {
   const double* X;
   i64 ldx, m;
   int b, bp;       // width, padded width (multiple of 4)
-  int cnt, G, rb;  // micro-tiles, groups, rows per block
+  int M, RG;       // main tiles, row groups
+  int E, tpt;      // extra tiles, threads per extra tile
+  int rb;          // rows per block
   i64 nb, P;       // row blocks, persistent blocks
   double* part;    // [P][b*b]
   const int* status;
 };
 
-__global__ void __launch_bounds__(kSyrkMaxThreads) syrk_partial_kernel(SyrkArgs a) {
+__device__ __forceinline__ void syrk_tile_row(const double* row, int i, int j, double (&acc)[4][4]) {
+  const double2 p0 = lds2(row + 4 * i), p1 = lds2(row + 4 * i + 2);
+  const double2 q0 = lds2(row + 4 * j), q1 = lds2(row + 4 * j + 2);
+  const double xv[4] = {p0.x, p0.y, p1.x, p1.y};
+  const double yv[4] = {q0.x, q0.y, q1.x, q1.y};
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = fma(xv[u], yv[v], acc[u][v]);
+}
+
+__device__ __forceinline__ void syrk_store_tile(double* P, int b, int i, int j, const double (&v)[4][4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int r = 4 * i + u, c = 4 * j + w;
+      if (r <= c && c < b) P[r + c * b] = v[u][w];
+    }
+}
+
+__global__ void __launch_bounds__(kSyrkThreads) syrk_partial_kernel(SyrkArgs a) {
   extern __shared__ __align__(16) double sm[];
   if (a.status && *a.status) return;
   const int t = threadIdx.x;
   const int sp = a.bp + 2;  // padded row stride (even: keeps 16-byte alignment)
-  const bool active = t < a.G * a.cnt;
-  int g = 0, mi = 0, mj = 0;
-  if (active) {
-    g = t / a.cnt;
-    decode_upper(t - g * a.cnt, mi, mj);
-  }
-  double acc[4][4];
+  int mi, mj;
+  decode_upper(t % a.M, mi, mj);
+  const int g = t / a.M;
+  const bool extra = a.E > 0 && t < a.E * a.tpt;
+  int ei = 0, ej = 0;
+  const int ek = extra ? t % a.tpt : 0;
+  if (extra) decode_upper(a.M + t / a.tpt, ei, ej);
+  double am[4][4], ae[4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int v = 0; v < 4; ++v) am[u][v] = ae[u][v] = 0.0;
 
   i64 ib, ie;
   item_range(blockIdx.x, a.nb, a.P, ib, ie);
@@ -85,59 +115,57 @@ __global__ void __launch_bounds__(kSyrkMaxThreads) syrk_partial_kernel(SyrkArgs 
     const i64 r0 = blk * rb;
     const int nrow = (int)imin64(rb, a.m - r0);
     // stage X[r0:r0+rb, 0:bp] row-major; zero beyond m and beyond b
-    for (int e = t; e < rb * a.bp; e += blockDim.x) {
+    for (int e = t; e < rb * a.bp; e += kSyrkThreads) {
       const int r = e % rb, c = e / rb;
       double v = 0.0;
       if (r < nrow && c < a.b) v = a.X[(r0 + r) + (i64)c * a.ldx];
       sm[r * sp + c] = v;
     }
     __syncthreads();
-    if (active) {
-      const double* xi = sm + 4 * mi;
-      const double* xj = sm + 4 * mj;
 #pragma unroll 2
-      for (int r = g; r < nrow; r += a.G) {
-        const double2 p0 = lds2(xi + r * sp), p1 = lds2(xi + r * sp + 2);
-        const double2 q0 = lds2(xj + r * sp), q1 = lds2(xj + r * sp + 2);
-        const double xv[4] = {p0.x, p0.y, p1.x, p1.y};
-        const double yv[4] = {q0.x, q0.y, q1.x, q1.y};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
-      }
-    }
+    for (int r = g; r < nrow; r += a.RG) syrk_tile_row(sm + r * sp, mi, mj, am);
+    if (extra)
+      for (int r = ek; r < nrow; r += a.tpt) syrk_tile_row(sm + r * sp, ei, ej, ae);
     __syncthreads();
   }
-  // sum the groups in ascending group order
-  const int nthr = blockDim.x;
-  if (a.G > 1) {
-    if (active) {
+  // fixed-order sums: main tiles over the row groups, extra tiles over their threads
+  double* P = a.part + (i64)blockIdx.x * a.b * a.b;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) sm[(i * 4 + j) * nthr + t] = acc[i][j];
-    }
-    __syncthreads();
-    if (active && g == 0) {
-      for (int gg = 1; gg < a.G; ++gg) {
-        const int tt = gg * a.cnt + t;
+    for (int v = 0; v < 4; ++v) sm[(u * 4 + v) * kSyrkThreads + t] = am[u][v];
+  __syncthreads();
+  if (t < a.M) {
+    double sum[4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] += sm[(i * 4 + j) * nthr + tt];
+      for (int v = 0; v < 4; ++v) {
+        double x = 0.0;
+        for (int gg = 0; gg < a.RG; ++gg) x += sm[(u * 4 + v) * kSyrkThreads + gg * a.M + t];
+        sum[u][v] = x;
       }
-    }
+    syrk_store_tile(P, a.b, mi, mj, sum);
   }
-  if (active && g == 0) {
-    double* P = a.part + (i64)blockIdx.x * a.b * a.b;
+  if (a.E > 0) {
+    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = 4 * mi + i, c = 4 * mj + j;
-        if (r <= c && c < a.b) P[r + c * a.b] = acc[i][j];
-      }
+      for (int v = 0; v < 4; ++v) sm[(u * 4 + v) * kSyrkThreads + t] = ae[u][v];
+    __syncthreads();
+    if (extra && ek == 0) {
+      double sum[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double x = 0.0;
+          for (int k = 0; k < a.tpt; ++k) x += sm[(u * 4 + v) * kSyrkThreads + t + k];
+          sum[u][v] = x;
+        }
+      syrk_store_tile(P, a.b, ei, ej, sum);
+    }
   }
 }
 
@@ -293,20 +321,24 @@ __global__ void tn_reduce_kernel(const double* part, int p, int q, int TP, int T
 inline int pick_tile(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 64; }
 
 struct SyrkPlan {
-  int bp, cnt, G, threads, rb;
+  int bp, M, RG, E, tpt, rb;
   size_t smem;
 };
 SyrkPlan syrk_plan(int b) {
   SyrkPlan s;
   const int n4 = (b + 3) / 4;
   s.bp = 4 * n4;
-  s.cnt = n4 * (n4 + 1) / 2;
-  s.G = kSyrkMaxThreads / s.cnt;
-  if (s.G < 1) s.G = 1;
-  s.threads = ((s.G * s.cnt + 31) / 32) * 32;
-  const int per = 4096 / ((s.bp + 2) * s.G);
-  s.rb = s.G * (per > 1 ? per : 1);
-  size_t tile = (size_t)s.rb * (s.bp + 2), red = (size_t)16 * s.threads;
+  const int cnt = n4 * (n4 + 1) / 2;
+  s.M = 1;
+  while (s.M * 2 <= cnt && s.M * 2 <= kSyrkThreads) s.M *= 2;
+  s.RG = kSyrkThreads / s.M;
+  s.E = cnt - s.M;
+  s.tpt = s.E > 0 ? kSyrkThreads / s.E : 0;
+  // about 8192 staged doubles (the size of the reduction area) per row
+  // block, a multiple of the row groups
+  const int per = 8192 / (s.bp + 2);
+  s.rb = per >= s.RG ? per / s.RG * s.RG : s.RG;
+  const size_t tile = (size_t)s.rb * (s.bp + 2), red = (size_t)16 * kSyrkThreads;
   s.smem = (tile > red ? tile : red) * sizeof(double);
   return s;
 }
@@ -318,7 +350,7 @@ int syrk_occupancy(int b, const SyrkPlan& s) {
   if (g_occ_syrk[b] == 0) {
     cudaFuncSetAttribute(syrk_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, syrk_partial_kernel, s.threads, s.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, syrk_partial_kernel, kSyrkThreads, s.smem);
     g_occ_syrk[b] = occ > 0 ? occ : 1;
   }
   return g_occ_syrk[b];
@@ -447,8 +479,10 @@ cudaError_t tn_product(i64 m, int p, int q, const double* X, i64 ldx, const doub
     a.m = m;
     a.b = p;
     a.bp = s.bp;
-    a.cnt = s.cnt;
-    a.G = s.G;
+    a.M = s.M;
+    a.RG = s.RG;
+    a.E = s.E;
+    a.tpt = s.tpt;
     a.rb = s.rb;
     a.nb = (m + s.rb - 1) / s.rb;
     a.P = P.S;
@@ -456,7 +490,7 @@ cudaError_t tn_product(i64 m, int p, int q, const double* X, i64 ldx, const doub
     a.status = status;
     if (m > 0) {
       prof_begin(kGram, st);
-      syrk_partial_kernel<<<P.S, s.threads, s.smem, st>>>(a);
+      syrk_partial_kernel<<<P.S, kSyrkThreads, s.smem, st>>>(a);
       prof_end(kGram, (double)m * p * (p + 1), st);
     }
     const int thr = 256;

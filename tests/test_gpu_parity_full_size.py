@@ -22,11 +22,13 @@ that CQR2GS needs about ten panels there (Sec. 5.3, Fig. 3); with 4 panels
 the oracle reaches only 1.7e-12 orthogonality at 2^18 x 256.
 
 2. The differentiable batch: 64 matrices, m uniform in [10^4, 10^5], n = 64,
-kappa = 1e4, b = 16, through qr_batched (one batched forward call, one
-adjoint per matrix).  Every Q_i, R_i and gradient is bitwise the single-call
-one (qr / backward with the same inputs), and four of the gradients match
-torch.linalg.qr's autograd, sign-normalised to a positive diagonal, within
-1e-9 (the bound of the single-matrix test at the same kappa).
+kappa = 1e4, b = 16, through qr_batched (one persistent batched forward
+launch, one adjoint per matrix).  Every Q_i, R_i is within the parity
+tolerances of the single call (1e-11), every gradient is bitwise
+backward(Q_i, R_i, Qbar_i, Rbar_i) on the batched factors, and four of the
+gradients match torch.linalg.qr's autograd, sign-normalised to a positive
+diagonal, within 1e-9 (the bound of the single-matrix test at the same
+kappa).
 """
 import numpy as np
 import pytest
@@ -148,8 +150,9 @@ def test_differentiable_batch_of_64(cuda_lib):
     torch.cuda.synchronize()
     for i, ((Q, R), A, dQ, dR) in enumerate(zip(outs, As, dQs, dRs)):
         Qs, Rs = P.factor(A.detach(), b)
-        assert torch.equal(Q, Qs) and torch.equal(R, Rs), i
-        assert torch.equal(A.grad, P.backward(Qs, Rs, dQ, dR)), i
+        assert (torch.linalg.norm(R - Rs) / torch.linalg.norm(Rs)).item() <= 1e-11, i
+        assert (Q - Qs).abs().max().item() <= 1e-11, i
+        assert torch.equal(A.grad, P.backward(Q.detach(), R.detach(), dQ, dR)), i
     for i in (0, 21, 42, 63):
         B = As[i].detach().clone().contiguous().requires_grad_(True)
         Qt, Rt = torch.linalg.qr(B)
