@@ -15,7 +15,8 @@
 // identical factors without a second barrier.
 //
 // Passes.  One panel step of Alg. 9 reads the rows it needs once per pass,
-// in sub-blocks of kBR rows staged in shared memory, and fuses the
+// in sub-blocks of 64 to 256 rows (more when fewer columns are loaded)
+// staged in shared memory, and fuses the
 // streaming operation with the next m-row sum:
 //   first pass    (copy A -> Q if out of place) + Gram of panel 1
 //   T1            Q_j = A_j S1^{-1}  + Gram (j = 1) or Z = Q_{1:j-1}^T P (j > 1)
@@ -57,7 +58,8 @@ namespace cqr {
 namespace {
 
 constexpr int kBT = 512;            // threads per CTA
-constexpr int kBR = 64;             // rows per staged sub-block
+constexpr int kBR = 64;             // rows per staged sub-block at full width (multiples of it below)
+constexpr int kBRMax = 4 * kBR;     // rows per staged sub-block for narrow passes
 constexpr int kBNMax = 128;         // widest matrix of the persistent path
 constexpr int kBSlot = 8448;        // doubles per partial slot: the Gram of b = 128 (528 tiles x 16)
 constexpr unsigned long long kBWaitNs = 2000000000ull;
@@ -98,7 +100,8 @@ struct Smem {
   double* dg;
   double* rv;
   double* M;
-  int ts;
+  int ts;   // row stride of the staged tile (set per pass)
+  int rb;   // rows of the staged tile (set per pass, a multiple of kBR)
 };
 
 __host__ __device__ inline int tile_stride(int nmax) { return nmax + 1; }
@@ -120,6 +123,7 @@ __device__ Smem carve(double* sm, int nmax, int bmax) {
   s.rv = s.dg + bmax;
   s.M = s.rv + bmax;
   s.ts = tile_stride(nmax);
+  s.rb = kBR;
   return s;
 }
 
@@ -133,6 +137,16 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// 8-byte asynchronous global -> shared copy; zero-fills when !valid (the
+// source is then not read).
+__device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
 // Group barrier, bounded in time.  Returns false (for every thread of the
@@ -227,20 +241,20 @@ __device__ __forceinline__ void acc_tile(const double* tile, int ts, int r, int 
 }
 
 // accumulate one staged sub-block (kBR rows, zero beyond the live rows)
-__device__ __forceinline__ void tn_accumulate(const TnMap& mp, const Smem& s, double (&am)[4][4],
+__device__ __forceinline__ void tn_accumulate(const TnMap& mp, const Smem& s, int nr, double (&am)[4][4],
                                               double (&ae)[4][4]) {
   const int t = threadIdx.x;
   {
     int i, j;
     tile_ij(mp, t % mp.M, i, j);
     const int xc = mp.xc + 4 * i, yc = mp.yc + 4 * j;
-    for (int r = t / mp.M; r < kBR; r += mp.RG) acc_tile(s.tile, s.ts, r, xc, yc, am);
+    for (int r = t / mp.M; r < nr; r += mp.RG) acc_tile(s.tile, s.ts, r, xc, yc, am);
   }
   if (mp.E > 0 && t < mp.E * mp.tpt) {
     int i, j;
     tile_ij(mp, mp.M + t / mp.tpt, i, j);
     const int xc = mp.xc + 4 * i, yc = mp.yc + 4 * j;
-    for (int r = t % mp.tpt; r < kBR; r += mp.tpt) acc_tile(s.tile, s.ts, r, xc, yc, ae);
+    for (int r = t % mp.tpt; r < nr; r += mp.tpt) acc_tile(s.tile, s.ts, r, xc, yc, ae);
   }
 }
 
@@ -284,73 +298,100 @@ __device__ void tn_flush(const TnMap& mp, const Smem& s, double (&am)[4][4], dou
 // C (tile columns [cc, cc+q)) -= X (tile columns [xc, xc+p)) * Mm (p x q,
 // row-major, leading dimension q), in place in the staged sub-block.  Each
 // thread owns a TR x TC block of C (the shape that keeps the most threads
-// busy); the sum starts from C and takes one fused multiply-add per term in
-// ascending k.
-__device__ void nn_update(const Smem& s, int xc, int p, int cc, int q, const double* Mm) {
-  int TR = 1, TC = 1, best = -1;
-  const int cand[8][2] = {{4, 4}, {4, 3}, {4, 2}, {2, 3}, {4, 1}, {1, 3}, {2, 1}, {1, 1}};
-  for (int k = 0; k < 8; ++k) {
-    const int tr = cand[k][0], tc = cand[k][1];
-    if (q % tc) continue;
-    const int thr = (kBR / tr) * (q / tc);
-    if (thr <= kBT && thr > best) {
-      best = thr;
-      TR = tr;
-      TC = tc;
-    }
-  }
+// busy, a template so that no multiply-add is issued for padding); the sum
+// starts from C and takes one fused multiply-add per term in ascending k.
+template <int TR, int TC>
+__device__ void nn_update_block(const Smem& s, int nr, int xc, int p, int cc, int q, const double* Mm) {
   const int t = threadIdx.x;
-  if (t >= best) return;
-  const int nrt = kBR / TR;
+  const int nrt = s.rb / TR;
+  if (t >= nrt * (q / TC)) return;
   const int r0 = (t % nrt) * TR, c0 = (t / nrt) * TC;
-  double acc[4][4];
+  if (r0 >= nr) return;  // padding rows only
+  double acc[TR][TC];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < TR; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = (u < TR && v < TC) ? s.tile[(size_t)(r0 + u) * s.ts + cc + c0 + v] : 0.0;
+    for (int v = 0; v < TC; ++v) acc[u][v] = s.tile[(size_t)(r0 + u) * s.ts + cc + c0 + v];
+#pragma unroll 2
   for (int k = 0; k < p; ++k) {
-    double x[4], mv[4];
+    double x[TR], mv[TC];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = u < TR ? s.tile[(size_t)(r0 + u) * s.ts + xc + k] : 0.0;
+    for (int u = 0; u < TR; ++u) x[u] = s.tile[(size_t)(r0 + u) * s.ts + xc + k];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) mv[v] = v < TC ? Mm[(size_t)k * q + c0 + v] : 0.0;
+    for (int v = 0; v < TC; ++v) mv[v] = Mm[(size_t)k * q + c0 + v];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < TR; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (u < TR && v < TC) acc[u][v] = fma(-x[u], mv[v], acc[u][v]);
+      for (int v = 0; v < TC; ++v) acc[u][v] = fma(-x[u], mv[v], acc[u][v]);
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < TR; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      if (u < TR && v < TC) s.tile[(size_t)(r0 + u) * s.ts + cc + c0 + v] = acc[u][v];
+    for (int v = 0; v < TC; ++v) s.tile[(size_t)(r0 + u) * s.ts + cc + c0 + v] = acc[u][v];
 }
 
-// Row-wise forward substitution on tile columns [tc, tc+b): q_c = (x_c -
-// sum_{i<c} q_i U_ic) / U_cc with the reciprocal rv[c]; U in s.U (row-major,
-// leading dimension b, diagonal and lower triangle zero).  L lanes of one
-// warp share a row; lane l owns the columns c = l (mod L).  Step c: the
-// owner scales column c, then every lane subtracts q_c U_{c,c'} from its
-// columns c' > c, in ascending c for each c' (the definition's order).
-__device__ void trsm_rows_staged(const Smem& s, int tc, int b) {
-  const int L = b >= 8 ? 8 : b;
+__device__ void nn_update(const Smem& s, int nr, int xc, int p, int cc, int q, const double* Mm) {
+  // the candidate shape with the most threads <= kBT (ties: the larger block)
+  int best = -1, pick = 7;
+  const int cand[8][2] = {{4, 4}, {4, 3}, {4, 2}, {2, 3}, {4, 1}, {1, 3}, {2, 1}, {1, 1}};
+  for (int k = 0; k < 8; ++k) {
+    if (q % cand[k][1]) continue;
+    const int thr = (s.rb / cand[k][0]) * (q / cand[k][1]);
+    if (thr <= kBT && thr > best) {
+      best = thr;
+      pick = k;
+    }
+  }
+  switch (pick) {
+    case 0: nn_update_block<4, 4>(s, nr, xc, p, cc, q, Mm); break;
+    case 1: nn_update_block<4, 3>(s, nr, xc, p, cc, q, Mm); break;
+    case 2: nn_update_block<4, 2>(s, nr, xc, p, cc, q, Mm); break;
+    case 3: nn_update_block<2, 3>(s, nr, xc, p, cc, q, Mm); break;
+    case 4: nn_update_block<4, 1>(s, nr, xc, p, cc, q, Mm); break;
+    case 5: nn_update_block<1, 3>(s, nr, xc, p, cc, q, Mm); break;
+    case 6: nn_update_block<2, 1>(s, nr, xc, p, cc, q, Mm); break;
+    default: nn_update_block<1, 1>(s, nr, xc, p, cc, q, Mm); break;
+  }
+}
+
+// Row-wise forward substitution on tile columns [tc, tc+b): with the rows
+// of U pre-scaled by the reciprocal diagonal (Ut_cc' = U_cc' / U_cc, see
+// prescale_rows), s_c' -= s_c Ut_cc' for c' > c in ascending c, then
+// q_c = s_c / U_cc (by the reciprocal rv[c]) -- q_c U_cc' = s_c Ut_cc', so
+// this is the substitution q_c = (x_c - sum_{i<c} q_i U_ic) / U_cc with
+// the division moved past the products.  L lanes of one warp share a row;
+// lane l owns the columns c = l (mod L).  Rows >= nr (padding) are skipped.
+__device__ void trsm_rows_staged(const Smem& s, int tc, int b, int nr) {
+  int L = kBT / s.rb;  // lanes per row: every thread busy, at most 8, at most b
+  L = L > 8 ? 8 : L;
+  L = L > b ? b : L;
   const int t = threadIdx.x;
-  const bool active = t < kBR * L;
   const int r = t / L, l = t % L;
+  const bool active = t < s.rb * L && r < nr;
   double* row = s.tile + (size_t)r * s.ts + tc;
-  const unsigned mask = __activemask();
   for (int c = 0; c < b; ++c) {
-    if (active && l == c % L) row[c] = row[c] * s.rv[c];
-    __syncwarp(mask);
+    __syncwarp();  // column c complete: its last update came at step c - 1
     if (active) {
       const double q = row[c];
       const double* urow = s.U + (size_t)c * b;
       for (int cp = (c + 1) / L * L + l; cp < b; cp += L)
         if (cp > c) row[cp] = fma(-q, urow[cp], row[cp]);
     }
-    __syncwarp(mask);
   }
+  __syncwarp();
+  if (active)
+    for (int c = l; c < b; c += L) row[c] *= s.rv[c];
+}
+
+// U_cc' := U_cc' / U_cc (by the reciprocal) for c' > c: the form the staged
+// substitution uses.  Called after the unscaled factor has been used for
+// the R products and saved.
+__device__ void prescale_rows(const Smem& s, int b) {
+  for (int e = threadIdx.x; e < b * b; e += kBT) {
+    const int c = e / b, cp = e % b;
+    if (cp > c) s.U[e] *= s.rv[c];
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -371,8 +412,18 @@ struct PassSpec {
   int x0, px, y0, qy;
 };
 
-__device__ void run_pass(const PassSpec& P, const Smem& s, i64 R0, i64 R1, double* slot) {
+__device__ void run_pass(const PassSpec& P, const Smem& s0, i64 R0, i64 R1, double* slot) {
   const int t = threadIdx.x;
+  // the tile for this pass: an odd row stride just above the loaded width,
+  // and as many 64-row groups (up to 4) as the staging area holds
+  Smem s = s0;
+  {
+    const int w = P.hi - P.lo;
+    s.ts = (w % 2 == 0) ? w + 1 : w + 2;
+    int groups = (int)(region0_doubles(s0.ts - 1) / ((size_t)kBR * s.ts));
+    groups = groups > kBRMax / kBR ? kBRMax / kBR : (groups < 1 ? 1 : groups);
+    s.rb = groups * kBR;
+  }
   TnMap mp{};
   if (P.op2 == 1) mp = make_map(1, P.gb, P.gb, P.g0 - P.lo, P.g0 - P.lo);
   if (P.op2 == 2) mp = make_map(0, P.px, P.qy, P.x0 - P.lo, P.y0 - P.lo);
@@ -382,23 +433,27 @@ __device__ void run_pass(const PassSpec& P, const Smem& s, i64 R0, i64 R1, doubl
 #pragma unroll
     for (int v = 0; v < 4; ++v) am[u][v] = ae[u][v] = 0.0;
   const int w = P.hi - P.lo;
-  for (i64 r0 = R0; r0 < R1; r0 += kBR) {
-    const int nr = (int)imin64(kBR, R1 - r0);
-    // stage rows (zero beyond nr): coalesced along the rows of each column
-    for (int e = t; e < kBR * w; e += kBT) {
-      const int r = e % kBR, c = e / kBR;
-      s.tile[(size_t)r * s.ts + c] = r < nr ? P.src[(r0 + r) + (i64)(P.lo + c) * P.lds] : 0.0;
+  const int rb = s.rb;
+  for (i64 r0 = R0; r0 < R1; r0 += rb) {
+    const int nr = (int)imin64(rb, R1 - r0);
+    // stage rows (zero beyond nr): asynchronous copies, coalesced along the
+    // rows of each column, all in flight before the one wait
+    for (int e = t; e < rb * w; e += kBT) {
+      const int r = e % rb, c = e / rb;
+      const bool ok = r < nr;
+      cp_async8(s.tile + (size_t)r * s.ts + c, ok ? P.src + (r0 + r) + (i64)(P.lo + c) * P.lds : P.src, ok);
     }
+    cp_async_wait_all();
     __syncthreads();
-    if (P.op1 == 1) trsm_rows_staged(s, P.t0 - P.lo, P.tb);
-    if (P.op1 == 2) nn_update(s, P.x0u - P.lo, P.pu, P.c0u - P.lo, P.qu, P.Mm);
+    if (P.op1 == 1) trsm_rows_staged(s, P.t0 - P.lo, P.tb, nr);
+    if (P.op1 == 2) nn_update(s, nr, P.x0u - P.lo, P.pu, P.c0u - P.lo, P.qu, P.Mm);
     __syncthreads();
     const int ws = P.st_hi - P.st_lo;
-    for (int e = t; e < kBR * ws; e += kBT) {
-      const int r = e % kBR, c = e / kBR;
+    for (int e = t; e < rb * ws; e += kBT) {
+      const int r = e % rb, c = e / rb;
       if (r < nr) P.dst[(r0 + r) + (i64)(P.st_lo + c) * P.ldd] = s.tile[(size_t)r * s.ts + (P.st_lo - P.lo) + c];
     }
-    if (P.op2) tn_accumulate(mp, s, am, ae);
+    if (P.op2) tn_accumulate(mp, s, nr, am, ae);
     __syncthreads();
   }
   if (P.op2) tn_flush(mp, s, am, ae, slot);
@@ -592,6 +647,8 @@ __global__ void __launch_bounds__(kBT, 1) batched_mcqr2gs_kernel(BArgs a) {
           s1g[e] = i <= c ? su(s, bw, i, c) : 0.0;
         }
       // ---- T1: P = A_j S1^{-1}, then the Gram of P (c0 == 0) or Z = Q_{1:j-1}^T P
+      __syncthreads();  // S1 saved from the unscaled factor
+      prescale_rows(s, bw);
       {
         my = slots[phase & 1] + (size_t)rank * kBSlot;
         PassSpec P{};
@@ -668,6 +725,8 @@ __global__ void __launch_bounds__(kBT, 1) batched_mcqr2gs_kernel(BArgs a) {
       }
       // ---- T2: Q_j = P S2^{-1}, then Y = Q_j^T A_{j+1:k}
       const int wn = n - c0 - bw;
+      __syncthreads();  // the R products used the unscaled factor
+      prescale_rows(s, bw);
       {
         my = slots[phase & 1] + (size_t)rank * kBSlot;
         PassSpec P{};

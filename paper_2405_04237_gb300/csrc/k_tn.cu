@@ -114,13 +114,17 @@ __global__ void __launch_bounds__(kSyrkThreads) syrk_partial_kernel(SyrkArgs a) 
   for (i64 blk = ib; blk < ie; ++blk) {
     const i64 r0 = blk * rb;
     const int nrow = (int)imin64(rb, a.m - r0);
-    // stage X[r0:r0+rb, 0:bp] row-major; zero beyond m and beyond b
+    // stage X[r0:r0+rb, 0:bp] row-major; zero beyond m and beyond b.
+    // Asynchronous copies: every load of the block is in flight before the
+    // one wait, instead of one memory latency per loop iteration.
     for (int e = t; e < rb * a.bp; e += kSyrkThreads) {
       const int r = e % rb, c = e / rb;
-      double v = 0.0;
-      if (r < nrow && c < a.b) v = a.X[(r0 + r) + (i64)c * a.ldx];
-      sm[r * sp + c] = v;
+      const bool ok = r < nrow && c < a.b;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(sm + r * sp + c);
+      const double* src = ok ? a.X + (r0 + r) + (i64)c * a.ldx : a.X;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 #pragma unroll 2
     for (int r = g; r < nrow; r += a.RG) syrk_tile_row(sm + r * sp, mi, mj, am);
@@ -241,18 +245,22 @@ __global__ void __launch_bounds__(kTnThreads) tn_partial_kernel(TnArgs a) {
     for (; item < tile_end; ++item) {
       const i64 r0 = (item - tile * a.nb) * Sh::RB;
       const int nrow = (int)imin64(Sh::RB, a.m - r0);
+      // asynchronous staging (zero-filled beyond m, p, q): all loads in flight before one wait
       for (int e = t; e < Sh::RB * TP; e += kTnThreads) {
         const int r = e % Sh::RB, c = e / Sh::RB;
-        double v = 0.0;
-        if (r < nrow && p0 + c < a.p) v = a.X[(r0 + r) + (i64)(p0 + c) * a.ldx];
-        Xs[r * Sh::SP + c] = v;
+        const bool ok = r < nrow && p0 + c < a.p;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Xs + r * Sh::SP + c);
+        const double* src = ok ? a.X + (r0 + r) + (i64)(p0 + c) * a.ldx : a.X;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
       }
       for (int e = t; e < Sh::RB * TQ; e += kTnThreads) {
         const int r = e % Sh::RB, c = e / Sh::RB;
-        double v = 0.0;
-        if (r < nrow && q0 + c < a.q) v = a.Y[(r0 + r) + (i64)(q0 + c) * a.ldy];
-        Ys[r * Sh::SQ + c] = v;
+        const bool ok = r < nrow && q0 + c < a.q;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Ys + r * Sh::SQ + c);
+        const double* src = ok ? a.Y + (r0 + r) + (i64)(q0 + c) * a.ldy : a.Y;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
       }
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
       __syncthreads();
       const double* xi = Xs + 4 * mi;
       const double* yj = Ys + 4 * mj;

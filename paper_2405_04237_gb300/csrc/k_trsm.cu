@@ -36,6 +36,16 @@ inline size_t trsm_smem(int b) {
   return sizeof(double) * ((size_t)b * kRows + (size_t)b * (b + 1) / 2 + kGrp + b);
 }
 
+// 8-byte asynchronous global -> shared copy (all of a block's staging loads
+// in flight before one wait, instead of one memory latency per iteration).
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void load_common(int b, const double* U, i64 ldu, const double* rinv, double* Up,
                                             double* rv) {
   const int t = threadIdx.x;
@@ -58,9 +68,10 @@ __global__ void __launch_bounds__(kRows) trsm_rows_kernel(i64 m, int b, double* 
   const int t = threadIdx.x;
   const i64 r0 = (i64)blockIdx.x * kRows;
   const int nrow = (int)imin64(kRows, m - r0);
-  load_common(b, U, ldu, rinv, Up, rv);
   if (t < nrow)
-    for (int c = 0; c < b; ++c) Ts[c * kRows + t] = X[r0 + t + (i64)c * ldx];
+    for (int c = 0; c < b; ++c) cp_async8(Ts + c * kRows + t, X + r0 + t + (i64)c * ldx);
+  load_common(b, U, ldu, rinv, Up, rv);
+  cp_async_wait_all();
   __syncthreads();
   if (t < nrow) {
     for (int g0 = 0; g0 < b; g0 += kGrp) {
@@ -100,9 +111,10 @@ __global__ void __launch_bounds__(kRows) trsm_rows_t_kernel(i64 m, int b, double
   const int t = threadIdx.x;
   const i64 r0 = (i64)blockIdx.x * kRows;
   const int nrow = (int)imin64(kRows, m - r0);
-  load_common(b, U, ldu, rinv, Up, rv);
   if (t < nrow)
-    for (int c = 0; c < b; ++c) Ts[c * kRows + t] = X[r0 + t + (i64)c * ldx];
+    for (int c = 0; c < b; ++c) cp_async8(Ts + c * kRows + t, X + r0 + t + (i64)c * ldx);
+  load_common(b, U, ldu, rinv, Up, rv);
+  cp_async_wait_all();
   __syncthreads();
   if (t < nrow) {
     // groups [g_lo, g_hi) from the right; s[k] holds column g_hi-1-k
