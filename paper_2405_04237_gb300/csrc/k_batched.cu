@@ -302,11 +302,11 @@ __device__ void tn_flush(const TnMap& mp, const Smem& s, double (&am)[4][4], dou
 // starts from C and takes one fused multiply-add per term in ascending k.
 template <int TR, int TC>
 __device__ void nn_update_block(const Smem& s, int nr, int xc, int p, int cc, int q, const double* Mm) {
-  const int t = threadIdx.x;
   const int nrt = s.rb / TR;
-  if (t >= nrt * (q / TC)) return;
-  const int r0 = (t % nrt) * TR, c0 = (t / nrt) * TC;
-  if (r0 >= nr) return;  // padding rows only
+  const int nblk = nrt * (q / TC);
+  for (int bi = threadIdx.x; bi < nblk; bi += kBT) {
+  const int r0 = (bi % nrt) * TR, c0 = (bi / nrt) * TC;
+  if (r0 >= nr) continue;  // padding rows only
   double acc[TR][TC];
 #pragma unroll
   for (int u = 0; u < TR; ++u)
@@ -328,10 +328,12 @@ __device__ void nn_update_block(const Smem& s, int nr, int xc, int p, int cc, in
   for (int u = 0; u < TR; ++u)
 #pragma unroll
     for (int v = 0; v < TC; ++v) s.tile[(size_t)(r0 + u) * s.ts + cc + c0 + v] = acc[u][v];
+  }
 }
 
 __device__ void nn_update(const Smem& s, int nr, int xc, int p, int cc, int q, const double* Mm) {
-  // the candidate shape with the most threads <= kBT (ties: the larger block)
+  // the candidate shape with the most threads <= kBT (ties: the larger block);
+  // 4 x 4 always fits (staged rows x loaded width <= the staging area)
   int best = -1, pick = 7;
   const int cand[8][2] = {{4, 4}, {4, 3}, {4, 2}, {2, 3}, {4, 1}, {1, 3}, {2, 1}, {1, 1}};
   for (int k = 0; k < 8; ++k) {
@@ -420,8 +422,9 @@ __device__ void run_pass(const PassSpec& P, const Smem& s0, i64 R0, i64 R1, doub
   {
     const int w = P.hi - P.lo;
     s.ts = (w % 2 == 0) ? w + 1 : w + 2;
-    int groups = (int)(region0_doubles(s0.ts - 1) / ((size_t)kBR * s.ts));
-    groups = groups > kBRMax / kBR ? kBRMax / kBR : (groups < 1 ? 1 : groups);
+    const int fit = (int)(region0_doubles(s0.ts - 1) / ((size_t)kBR * s.ts));
+    int groups = 1;  // 1, 2 or 4 groups of 64 rows, so that the solve's lanes x rows fill the block
+    while (groups * 2 <= fit && groups * 2 <= kBRMax / kBR) groups *= 2;
     s.rb = groups * kBR;
   }
   TnMap mp{};
@@ -463,9 +466,18 @@ __device__ void run_pass(const PassSpec& P, const Smem& s0, i64 R0, i64 R1, doub
 __device__ __forceinline__ double slot_sum(const double* slots, int G, int sym, int tp, int a, int c) {
   const int i = a / 4, j = c / 4;
   const int id = sym ? j * (j + 1) / 2 + i : i + j * tp;
-  const size_t off = (size_t)id * 16 + (a % 4) * 4 + (c % 4);
+  const double* p = slots + (size_t)id * 16 + (a % 4) * 4 + (c % 4);
   double v = 0.0;
-  for (int g = 0; g < G; ++g) v += slots[(size_t)g * kBSlot + off];
+  int g = 0;
+  for (; g + 4 <= G; g += 4) {  // four loads in flight, added in rank order
+    const double x0 = p[(size_t)g * kBSlot], x1 = p[(size_t)(g + 1) * kBSlot];
+    const double x2 = p[(size_t)(g + 2) * kBSlot], x3 = p[(size_t)(g + 3) * kBSlot];
+    v += x0;
+    v += x1;
+    v += x2;
+    v += x3;
+  }
+  for (; g < G; ++g) v += p[(size_t)g * kBSlot];
   return v;
 }
 
@@ -710,18 +722,36 @@ __global__ void __launch_bounds__(kBT, 1) batched_mcqr2gs_kernel(BArgs a) {
         failed = true;
         break;
       }
-      // R_jj = S2 S1 and (c0 > 0) R_{1:j-1,j} += Z S1, column slices of this rank
-      for (int c = rank; c < bw; c += a.G) {
-        for (int r = t; r <= c; r += kBT) {
-          double v = 0.0;
-          for (int i = r; i <= c; ++i) v = fma(su(s, bw, r, i), s1g[(size_t)c * bw + i], v);
-          mt.R[(c0 + r) + (i64)(c0 + c) * n] = v;
+      // R_jj = S2 S1 and (c0 > 0) R_{1:j-1,j} += Z S1, column slices of this
+      // rank; S1's upper triangle staged (packed by columns) in the tile area
+      {
+        double* s1p = s.tile;
+        for (int e = t; e < bw * (bw + 1) / 2; e += kBT) {
+          int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          while ((c + 1) * (c + 2) / 2 <= e) ++c;
+          while (c * (c + 1) / 2 > e) --c;
+          const int i = e - c * (c + 1) / 2;
+          s1p[e] = s1g[(size_t)c * bw + i];
         }
-        for (int r = t; r < c0; r += kBT) {
-          double v = mt.R[r + (i64)(c0 + c) * n];
-          for (int i = 0; i <= c; ++i) v = fma(s.M[(size_t)r * bw + i], s1g[(size_t)c * bw + i], v);
-          mt.R[r + (i64)(c0 + c) * n] = v;
+        __syncthreads();
+        const int ncol = (bw - rank + a.G - 1) / a.G;  // this rank's columns c = rank + G * k
+        const int per = c0 + bw;                       // rows of R above and on the diagonal block
+        for (int e = t; e < ncol * per; e += kBT) {
+          const int c = rank + a.G * (e / per), r = e % per;
+          const double* s1c = s1p + c * (c + 1) / 2;  // S1[0..c][c]
+          if (r >= c0) {  // R_jj entry (r - c0, c), on or above the diagonal
+            const int rr = r - c0;
+            if (rr > c) continue;
+            double v = 0.0;
+            for (int i = rr; i <= c; ++i) v = fma(su(s, bw, rr, i), s1c[i], v);
+            mt.R[(c0 + rr) + (i64)(c0 + c) * n] = v;
+          } else {
+            double v = mt.R[r + (i64)(c0 + c) * n];
+            for (int i = 0; i <= c; ++i) v = fma(s.M[(size_t)r * bw + i], s1c[i], v);
+            mt.R[r + (i64)(c0 + c) * n] = v;
+          }
         }
+        __syncthreads();
       }
       // ---- T2: Q_j = P S2^{-1}, then Y = Q_j^T A_{j+1:k}
       const int wn = n - c0 - bw;
