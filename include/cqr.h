@@ -116,7 +116,7 @@ enum cqr_variant {
  *   cqr_alloc_fn(bytes, stream, ctx) returns DEVICE memory of at least
  *     `bytes`, 256-byte aligned, usable on `stream` (NULL = failure);
  *   cqr_free_fn(ptr, bytes, stream, ctx) takes it back.
- * A call with workspace = NULL (cqr_factor, cqr_backward,
+ * A call with workspace = NULL (cqr_factor, cqr_factor_host, cqr_backward,
  * cqr_factor_batched) asks for exactly the *_workspace_size() bytes,
  * enqueues its work, SYNCHRONISES `stream`, then frees the memory -- so any
  * allocator works (cudaMalloc/cudaFree, a caching allocator, a pool), and
@@ -220,6 +220,46 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
 #define CQR_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int cqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double* Q, int64_t ldq, double* R,
                        int64_t ldr, int variant, int* status, cqr_stream_t stream);
+
+/*
+ * cqr_factor_host: A = Q R with A, Q and R in HOST memory; the library moves
+ * them to and from the caller's device buffers and overlaps those copies with
+ * the factorisation.  The paper times factorisations of resident matrices;
+ * this is the call for a matrix that lives in host memory.
+ *   Arguments 1-10 as in cqr_factor, but A, Q and R are host pointers
+ *   (column-major, leading dimensions lda, ldq, ldr).  Q may be A itself
+ *   (ldq == lda); otherwise the two must not overlap (-6).
+ *   Qd, ldqd   DEVICE buffer, m x n, ldqd >= m: receives A, is factored in
+ *              place and holds Q on return                          (args 11, 12)
+ *   Rd, ldrd   DEVICE buffer, n x n, ldrd >= n: holds R on return; must not
+ *              overlap Qd                                            (args 13, 14)
+ *   workspace, ws_bytes, stream  as in cqr_factor, sized by the same
+ *              cqr_workspace_size(m, n, panel_b, variant)          (args 15-17)
+ * Schedule for CQR_MCQR2GS (Alg. 9), on `stream` and one library-owned copy
+ * stream per device: the first panel's b columns are copied in first and its
+ * CholeskyQR2 (step 1) starts as soon as they have arrived, while the other
+ * n - b columns are copied in behind it; the first projection (steps 3-5)
+ * waits for them.  Each panel Q_j is final after its second CholeskyQR
+ * (step 8) and is never written again, so it is copied out at once, while
+ * later panels compute; R is copied out at the end.  Only the first panel's
+ * copy in and the last panel's copy out are not hidden.  The other variants
+ * copy A in, factor and copy Q and R out, in that order.  The kernels and
+ * their order are those of cqr_factor with the same arguments, so Qd, Rd and
+ * the host results are bitwise cqr_factor's.  Page-locked host buffers
+ * (cudaHostAlloc, cudaHostRegister) are needed for the overlap; pageable ones
+ * give the same results, but the CUDA runtime then makes the copies
+ * synchronous, so the host waits for each one.
+ * Returns the argument codes of cqr_factor (-3: A == NULL; -6: Q == NULL or
+ * overlapping A; -8: R == NULL), -13 (Qd == NULL), -14 (ldqd < m), -15
+ * (Rd == NULL or overlapping Qd), -16 (ldrd < n), or CQR_ERR_CUDA.  Like
+ * cqr_factor it returns once the work is enqueued (the host results are
+ * complete when `stream` is); with CQR_HALVE, or with workspace == NULL, it
+ * synchronises `stream` first.  The status word is left in the workspace
+ * (cqr_read_status), or returned for workspace == NULL.
+ */
+int cqr_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int panel_b, double* Q, int64_t ldq,
+                    double* R, int64_t ldr, int variant, double* Qd, int64_t ldqd, double* Rd, int64_t ldrd,
+                    void* workspace, size_t ws_bytes, cqr_stream_t stream);
 
 /*
  * cqr_read_panel_width: synchronises `stream`, then copies into *panel_b
@@ -411,6 +451,29 @@ int cqr_probe_fp64(int kind, int iters, double* gflops, double* flop_per_clk_sm,
  *   2 M N K).  Returns 0, -1 for a bad argument, CQR_ERR_CUDA on error.
  * cqr_kernel_class_name: static name of a kernel class.
  */
+/*
+ * Tracing.  The enqueue of every call brackets its phases with NVTX ranges
+ * (domain "cqr"; no cost unless a tool such as Nsight Systems is attached):
+ *   mCQR2GS (Alg. 9), panel j = 0 .. k-1 (with CQR_HALVE: the panel's first
+ *   column):  "cqr2_first_panel" 0 (step 1), then for j >= 1
+ *   "project_update" (steps 3-5: Y = Q_{j-1}^T A_{j:k}, A_{j:k} -= Q_{j-1} Y),
+ *   "cqr" (step 6), "reorthogonalise" (step 7), "cqr_final" (step 8),
+ *   "r_update" (R_jj = S2 S1, R_{1:j-1,j} += Z S1); with CQR_HALVE each
+ *   attempt of a panel's first CholeskyQR is "panel_test";
+ *   CQR2GS (Alg. 7): "cqrgs_pass" 0 and 1 (Alg. 6 twice), each holding
+ *   "cqr" j and "project_update" j per panel, then "r_update" -1;
+ *   CholeskyQR2 / shifted CholeskyQR3: "cqr2" / "scqr3" with panel -1;
+ *   cqr_factor_batched: "batched" with panel = batch size; cqr_backward:
+ *   "backward" -1.
+ * The ranges time the host-side enqueue (the kernels run asynchronously;
+ * a tool correlates them with the launches inside each range).
+ * cqr_set_trace(fn, ctx): also call fn(phase, panel, begin, ctx) on the
+ *   enqueueing thread at the start (begin = 1) and end (begin = 0) of every
+ *   phase; fn = NULL unregisters.  Returns 0.
+ */
+typedef void (*cqr_trace_fn)(const char* phase, int panel, int begin, void* ctx);
+int cqr_set_trace(cqr_trace_fn fn, void* ctx);
+
 unsigned long long cqr_launch_count(void);
 int cqr_profile_enable(int capacity);
 int cqr_profile_disable(void);

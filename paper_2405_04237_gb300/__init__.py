@@ -26,7 +26,7 @@ __all__ = [
     "factor", "qr", "backward", "factor_batched", "workspace_size", "default_panel",
     "CQRFunction", "CQRError", "read_status", "probe_fp64_peak", "probe_fp64", "colmajor", "empty_colmajor",
     "launch_count", "KernelTimer", "BatchedGraph", "batched_workspace_size", "qr_batched", "CQRBatchedFunction",
-    "use_torch_allocator", "read_panel_width", "batched_panel_widths",
+    "use_torch_allocator", "read_panel_width", "batched_panel_widths", "factor_host", "empty_colmajor_pinned", "PhaseTrace",
 ]
 
 
@@ -209,6 +209,69 @@ def factor(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, inplace: boo
         s = read_status(workspace, stream)
         if s != 0:
             raise CQRError(s, "cqr_factor")
+    return Q, R
+
+
+def empty_colmajor_pinned(m: int, n: int) -> torch.Tensor:
+    """A page-locked host m x n column-major FP64 matrix (for factor_host)."""
+    return torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+
+
+def factor_host(A: torch.Tensor, panel_b: int = 0, variant="mcqr2gs", *, out=None, device_out=None,
+                workspace: torch.Tensor | None = None, stream=None, lookahead: bool = False, adaptive: bool = False,
+                emulated: bool = False, halving: bool = False, check: bool = True, info: dict | None = None,
+                device=None):
+    """A = Q R for a HOST matrix A (CPU float64, column-major; page-locked
+    for the copy overlap).  The library copies A to the device buffer Qd,
+    factors it there and copies Q and R back, the copies overlapped with the
+    factorisation (cqr_factor_host).  out=(Q, R): host outputs (default: new
+    page-locked column-major matrices; Q may be A itself).  device_out=(Qd,
+    Rd): the CUDA buffers the factorisation runs in (default: new ones on
+    `device`, else the current device).  The remaining options are factor()'s.
+    Returns the host (Q, R); with check=False the call is asynchronous and
+    they are complete once `stream` is."""
+    if A.is_cuda or A.dtype != torch.float64 or A.dim() != 2:
+        raise ValueError("factor_host takes a CPU float64 matrix")
+    L = load()
+    m, n = A.shape
+    Ac = colmajor(A)
+    if out is not None:
+        Q, R = out
+    else:
+        Q, R = empty_colmajor_pinned(m, n), empty_colmajor_pinned(n, n)
+    for t in (Q, R):
+        if t.is_cuda or t.dtype != torch.float64 or colmajor(t).data_ptr() != t.data_ptr():
+            raise ValueError("host outputs must be column-major CPU float64 matrices")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if device_out is not None:
+        Qd, Rd = device_out
+    else:
+        Qd, Rd = empty_colmajor(m, n, dev), empty_colmajor(n, n, dev)
+    for t in (Qd, Rd):
+        _check_input(t)
+        if colmajor(t).data_ptr() != t.data_ptr():
+            raise ValueError("device buffers must be column-major")
+    flags = _variant(variant) | (_capi.LOOKAHEAD if lookahead else 0) | (_capi.ADAPTIVE if adaptive else 0) | (
+        _capi.EMULATED if emulated else 0) | (_capi.HALVE if halving else 0)
+    ws_bytes = L.cqr_workspace_size(m, n, int(panel_b), flags)
+    if ws_bytes == 0:
+        raise CQRError(-5 if n > 0 and m >= n else -1, "cqr_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=Qd.device)
+    elif workspace.numel() < ws_bytes:
+        raise ValueError(f"workspace too small: {workspace.numel()} < {ws_bytes}")
+    st = _stream(stream)
+    rc = L.cqr_factor_host(m, n, _ptr(Ac), _ld(Ac), int(panel_b), _ptr(Q), _ld(Q), _ptr(R), _ld(R), flags,
+                           _ptr(Qd), _ld(Qd), _ptr(Rd), _ld(Rd), _ptr(workspace),
+                           ctypes.c_size_t(workspace.numel()), st)
+    if rc != 0:
+        raise CQRError(rc, "cqr_factor_host")
+    if halving and info is not None:
+        info["panel_b"] = read_panel_width(workspace, stream)
+    if check:
+        s = read_status(workspace, stream)
+        if s != 0:
+            raise CQRError(s, "cqr_factor_host")
     return Q, R
 
 
@@ -429,6 +492,33 @@ def probe_fp64(kind: str = "dfma", iters: int = 100000) -> dict:
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(load().cqr_launch_count())
+
+
+class PhaseTrace:
+    """Context manager: records the phase ranges the library brackets its
+    enqueue with (the same ranges it emits as NVTX, domain "cqr") as
+    (phase, panel, begin) tuples in ``.events``, through cqr_set_trace."""
+
+    def __init__(self):
+        self.events = []
+        self._cb = None
+
+    def __enter__(self):
+        def _cb(name, panel, begin, ctx):
+            self.events.append((name.decode(), int(panel), int(begin)))
+
+        self._cb = _capi.TRACE_FN(_cb)
+        load().cqr_set_trace(self._cb, None)
+        return self
+
+    def __exit__(self, *exc):
+        load().cqr_set_trace(_capi.TRACE_FN(), None)
+        self._cb = None
+        return False
+
+    def phases(self):
+        """The (phase, panel) pairs in the order they began."""
+        return [(n, p) for n, p, b in self.events if b]
 
 
 class KernelTimer:

@@ -32,13 +32,14 @@ ERR_NOALLOC_TOO_LARGE = -3000
 ERR_ALLOC = -4000
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+TRACE_FN = ctypes.CFUNCTYPE(None, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTS = [
     "cqr_workspace_size", "cqr_default_panel", "cqr_factor", "cqr_read_status", "cqr_read_panel_width", "cqr_set_allocator",
     "cqr_backward_workspace_size", "cqr_backward", "cqr_batched_workspace_size",
     "cqr_factor_batched", "cqr_status_string", "cqr_probe_fp64_peak", "cqr_probe_fp64",
-    "cqr_factor_noalloc", "cqr_test_arm_wait_expiry", "cqr_test_arm_barrier_expiry", "cqr_batched_panel_widths", "cqr_launch_count", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
+    "cqr_factor_noalloc", "cqr_factor_host", "cqr_test_arm_wait_expiry", "cqr_test_arm_barrier_expiry", "cqr_batched_panel_widths", "cqr_launch_count", "cqr_set_trace", "cqr_profile_enable", "cqr_profile_disable", "cqr_profile_read", "cqr_kernel_class_name",
 ]
 KERNEL_CLASSES = ["gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm", "misc",
                   "batched"]
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True):
             "cqr_read_panel_width": (c_int, [vp, vp, PI]),
             "cqr_set_allocator": (c_int, [ALLOC_FN, FREE_FN, vp]),
             "cqr_factor_noalloc": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, vp, vp]),
+            "cqr_factor_host": (c_int, [i64, i64, dp, i64, c_int, dp, i64, dp, i64, c_int, dp, i64, dp, i64, vp, sz, vp]),
             "cqr_backward_workspace_size": (sz, [i64, i64]),
             "cqr_backward": (c_int, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64, vp, sz, vp]),
             "cqr_batched_workspace_size": (sz, [c_int, P64, P64, PI, c_int]),
@@ -92,6 +94,7 @@ def load(build_if_missing: bool = True):
             "cqr_test_arm_barrier_expiry": (c_int, [c_int, c_int, c_int, ctypes.c_longlong]),
             "cqr_batched_panel_widths": (c_int, [c_int, vp, vp, PI]),
             "cqr_launch_count": (ctypes.c_ulonglong, []),
+            "cqr_set_trace": (c_int, [TRACE_FN, vp]),
             "cqr_profile_enable": (c_int, [c_int]),
             "cqr_profile_disable": (c_int, []),
             "cqr_profile_read": (c_int, [c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),

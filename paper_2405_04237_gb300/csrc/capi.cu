@@ -230,9 +230,13 @@ cudaError_t cqrgs_run(i64 m, i64 n, int b, double* X, i64 ldx, double* R, i64 ld
   for (i64 j = 0; j < k; ++j) {
     const i64 jb = j * b;
     double* Xj = X + jb * ldx;
-    TRY(cqr_panel(m, b, Xj, ldx, R + jb + jb * ldr, ldr, w, (int)jb, 0, st));
+    {
+      TracePhase ph("cqr", (int)j);
+      TRY(cqr_panel(m, b, Xj, ldx, R + jb + jb * ldr, ldr, w, (int)jb, 0, st));
+    }
     const i64 wd = n - jb - b;
     if (wd > 0) {
+      TracePhase ph("project_update", (int)j);
       TRY(join_side(st, side, &pending));  // the rest of the previous update
       double* Yp = R + jb + (jb + b) * ldr;  // Y lands in R_{j,j+1:k}
       TRY(tn_product(m, b, (int)wd, Xj, ldx, Xj + (i64)b * ldx, ldx, 0, w.part, Yp, ldr, w.status, st));
@@ -242,46 +246,99 @@ cudaError_t cqrgs_run(i64 m, i64 n, int b, double* X, i64 ldx, double* R, i64 ld
   return join_side(st, side, &pending);
 }
 
+// Host-buffer factorisation (cqr_factor_host): the copy stream that brings
+// A's columns after the first panel in and takes every finished Q panel out.
+struct HostIO {
+  cudaStream_t cs;
+  cudaEvent_t fork, in_done, panel_done, join;
+  double* Qh;  // host destination of Q
+  i64 ldqh;
+  bool rest_pending;  // the main stream has not yet waited for in_done
+};
+
+// Columns [c0, c0 + w) of an m-row column-major matrix between two buffers
+// (one copy; a 1-D copy when both are packed).
+cudaError_t copy_cols(double* dst, i64 ldd, const double* src, i64 lds, i64 m, i64 c0, i64 w, cudaMemcpyKind kind,
+                      cudaStream_t s) {
+  if (w <= 0) return cudaSuccess;
+  if (ldd == m && lds == m)
+    return cudaMemcpyAsync(dst + c0 * ldd, src + c0 * lds, sizeof(double) * m * w, kind, s);
+  return cudaMemcpy2DAsync(dst + c0 * ldd, sizeof(double) * ldd, src + c0 * lds, sizeof(double) * lds,
+                           sizeof(double) * m, w, kind, s);
+}
+
+// Before the first m-row product that reads columns past the first panel.
+cudaError_t io_wait_rest(HostIO* io, cudaStream_t st) {
+  if (!io || !io->rest_pending) return cudaSuccess;
+  io->rest_pending = false;
+  return cudaStreamWaitEvent(st, io->in_done, 0);
+}
+
+// Q's columns [c0, c0 + w) are final (Alg. 9 step 1 / step 8) and no later
+// kernel writes them: copy them out behind the work enqueued so far.
+cudaError_t io_panel_out(HostIO* io, i64 m, const double* Q, i64 ldq, i64 c0, i64 w, cudaStream_t st) {
+  if (!io) return cudaSuccess;
+  TRY(cudaEventRecord(io->panel_done, st));
+  TRY(cudaStreamWaitEvent(io->cs, io->panel_done, 0));
+  return copy_cols(io->Qh, io->ldqh, Q, ldq, m, c0, w, cudaMemcpyDeviceToHost, io->cs);
+}
+
 // Alg. 9 on Q (m x n, in place); R (ldr) pre-zeroed.
 cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w, cudaStream_t st,
-                        const Side* side, bool adaptive) {
+                        const Side* side, bool adaptive, HostIO* io = nullptr) {
   const i64 k = n / b;
   bool pending = false;
-  // step 1: [Q_1, R_11] = CQR2(A_1)
-  TRY(cqr_panel(m, b, Q, ldq, w.S1, b, w, 0, 0, st));
-  TRY(cqr_panel(m, b, Q, ldq, w.S2, b, w, 0, 0, st, adaptive));
-  TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R, ldr, 1.0, 0, 1, 1, w.status, st));
+  {  // step 1: [Q_1, R_11] = CQR2(A_1)
+    TracePhase ph("cqr2_first_panel", 0);
+    TRY(cqr_panel(m, b, Q, ldq, w.S1, b, w, 0, 0, st));
+    TRY(cqr_panel(m, b, Q, ldq, w.S2, b, w, 0, 0, st, adaptive));
+    TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R, ldr, 1.0, 0, 1, 1, w.status, st));
+    TRY(io_panel_out(io, m, Q, ldq, 0, b, st));
+  }
   for (i64 j = 1; j < k; ++j) {
     const i64 jb = j * b, wd = n - jb;
     const double* Qprev = Q + (jb - b) * ldq;
     double* Aj = Q + jb * ldq;
     double* Yp = R + (jb - b) + jb * ldr;
-    // steps 3-5: Y = Q_{j-1}^T A_{j:k}; A_{j:k} -= Q_{j-1} Y; R_{j-1,j:k} = Y
-    TRY(join_side(st, side, &pending));
-    if (w.oz)
-      TRY(tn_product_emulated(m, b, (int)wd, Qprev, ldq, Aj, ldq, w.oz, Yp, ldr, w.status, st));
-    else
-      TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
-    if (w.oz)  // the emulated update uses w.oz, so it stays on this stream (no look-ahead split)
-      TRY(nn_update_emulated(m, (int)wd, b, Qprev, ldq, Yp, ldr, Aj, ldq, w.oz, w.status, st));
-    else
-      TRY(split_update(m, b, wd, Qprev, ldq, Yp, ldr, Aj, ldq, w.status, st, side, &pending));
-    // step 6: [P, S1] = CQR(A_j)
-    TRY(cqr_panel(m, b, Aj, ldq, w.S1, b, w, (int)jb, 0, st));
-    // step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z
-    if (w.oz)
-      TRY(tn_product_emulated(m, (int)jb, b, Q, ldq, Aj, ldq, w.oz, w.Z, jb, w.status, st));
-    else
-      TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
-    if (w.oz)
-      TRY(nn_update_emulated(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, w.oz, w.status, st));
-    else
-      TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
-    // step 8: [Q_j, S2] = CQR(P)
-    TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st, adaptive));
-    // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
-    TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R + jb + jb * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
-    TRY(nn_product(jb, b, b, w.Z, jb, w.S1, b, R + jb * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
+    const int pj = (int)j;
+    {  // steps 3-5: Y = Q_{j-1}^T A_{j:k}; A_{j:k} -= Q_{j-1} Y; R_{j-1,j:k} = Y
+      TracePhase ph("project_update", pj);
+      TRY(join_side(st, side, &pending));
+      TRY(io_wait_rest(io, st));
+      if (w.oz)
+        TRY(tn_product_emulated(m, b, (int)wd, Qprev, ldq, Aj, ldq, w.oz, Yp, ldr, w.status, st));
+      else
+        TRY(tn_product(m, b, (int)wd, Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
+      if (w.oz)  // the emulated update uses w.oz, so it stays on this stream (no look-ahead split)
+        TRY(nn_update_emulated(m, (int)wd, b, Qprev, ldq, Yp, ldr, Aj, ldq, w.oz, w.status, st));
+      else
+        TRY(split_update(m, b, wd, Qprev, ldq, Yp, ldr, Aj, ldq, w.status, st, side, &pending));
+    }
+    {  // step 6: [P, S1] = CQR(A_j)
+      TracePhase ph("cqr", pj);
+      TRY(cqr_panel(m, b, Aj, ldq, w.S1, b, w, (int)jb, 0, st));
+    }
+    {  // step 7: Z = Q_{1:j-1}^T P; P -= Q_{1:j-1} Z
+      TracePhase ph("reorthogonalise", pj);
+      if (w.oz)
+        TRY(tn_product_emulated(m, (int)jb, b, Q, ldq, Aj, ldq, w.oz, w.Z, jb, w.status, st));
+      else
+        TRY(tn_product(m, (int)jb, b, Q, ldq, Aj, ldq, 0, w.part, w.Z, jb, w.status, st));
+      if (w.oz)
+        TRY(nn_update_emulated(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, w.oz, w.status, st));
+      else
+        TRY(nn_product(m, b, (int)jb, Q, ldq, w.Z, jb, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
+    }
+    {  // step 8: [Q_j, S2] = CQR(P)
+      TracePhase ph("cqr_final", pj);
+      TRY(cqr_panel(m, b, Aj, ldq, w.S2, b, w, (int)jb, 0, st, adaptive));
+      TRY(io_panel_out(io, m, Q, ldq, jb, b, st));
+    }
+    {  // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
+      TracePhase ph("r_update", pj);
+      TRY(nn_product(b, b, b, w.S2, b, w.S1, b, R + jb + jb * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
+      TRY(nn_product(jb, b, b, w.Z, jb, w.S1, b, R + jb * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
+    }
   }
   return join_side(st, side, &pending);
 }
@@ -294,17 +351,21 @@ cudaError_t mcqr2gs_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 
 // rule as the oracle's or_mcqr2gs_halving; one host synchronisation per
 // attempt.  *b_final receives the last panel's width.
 cudaError_t mcqr2gs_halving_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, const Work& w,
-                                cudaStream_t st, bool adaptive, int* b_final) {
+                                cudaStream_t st, bool adaptive, int* b_final, HostIO* io = nullptr) {
   int bw = b, bprev = 0;
   for (i64 c0 = 0; c0 < n;) {
     double* Aj = Q + c0 * ldq;
+    const int pc = (int)c0;
     if (c0 > 0) {  // steps 3-5 with the previous panel (its own width)
+      TracePhase ph("project_update", pc);
+      TRY(io_wait_rest(io, st));
       const double* Qprev = Q + (c0 - bprev) * ldq;
       double* Yp = R + (c0 - bprev) + c0 * ldr;
       TRY(tn_product(m, bprev, (int)(n - c0), Qprev, ldq, Aj, ldq, 0, w.part, Yp, ldr, w.status, st));
       TRY(nn_product(m, (int)(n - c0), bprev, Qprev, ldq, Yp, ldr, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
     }
     for (;;) {  // the first CholeskyQR's Gram and Cholesky, with the panel test
+      TracePhase ph("panel_test", pc);
       int rej = 0;
       TRY(cudaMemsetAsync(w.skip, 0, sizeof(int), st));
       TRY(tn_product(m, bw, bw, Aj, ldq, Aj, ldq, 1, w.part, w.W, bw, w.status, st));
@@ -314,16 +375,25 @@ cudaError_t mcqr2gs_halving_run(i64 m, i64 n, int b, double* Q, i64 ldq, double*
       if (!rej) break;
       bw = halved_width(bw);
     }
-    TRY(trsm_any(m, bw, Aj, ldq, w.S1, bw, w.rinv, w.status, st));
+    {
+      TracePhase ph(c0 > 0 ? "cqr" : "cqr2_first_panel", pc);
+      TRY(trsm_any(m, bw, Aj, ldq, w.S1, bw, w.rinv, w.status, st));
+    }
     if (c0 > 0) {  // step 7
+      TracePhase ph("reorthogonalise", pc);
       TRY(tn_product(m, (int)c0, bw, Q, ldq, Aj, ldq, 0, w.part, w.Z, c0, w.status, st));
       TRY(nn_product(m, bw, (int)c0, Q, ldq, w.Z, c0, Aj, ldq, -1.0, 1, 0, 0, w.status, st));
     }
-    // step 1's second pass / step 8
-    TRY(cqr_panel(m, bw, Aj, ldq, w.S2, bw, w, (int)c0, 0, st, adaptive));
-    // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
-    TRY(nn_product(bw, bw, bw, w.S2, bw, w.S1, bw, R + c0 + c0 * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
-    if (c0 > 0) TRY(nn_product(c0, bw, bw, w.Z, c0, w.S1, bw, R + c0 * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
+    {  // step 1's second pass / step 8
+      TracePhase ph(c0 > 0 ? "cqr_final" : "cqr2_first_panel", pc);
+      TRY(cqr_panel(m, bw, Aj, ldq, w.S2, bw, w, (int)c0, 0, st, adaptive));
+      TRY(io_panel_out(io, m, Q, ldq, c0, bw, st));
+    }
+    {  // R_jj = S2 S1;  R_{1:j-1,j} += Z S1
+      TracePhase ph("r_update", pc);
+      TRY(nn_product(bw, bw, bw, w.S2, bw, w.S1, bw, R + c0 + c0 * ldr, ldr, 1.0, 0, 1, 1, w.status, st));
+      if (c0 > 0) TRY(nn_product(c0, bw, bw, w.Z, c0, w.S1, bw, R + c0 * ldr, ldr, 1.0, 1, 0, 1, w.status, st));
+    }
     bprev = bw;
     c0 += bw;
   }
@@ -332,26 +402,38 @@ cudaError_t mcqr2gs_halving_run(i64 m, i64 n, int b, double* Q, i64 ldq, double*
 }
 
 cudaError_t factor_run(i64 m, i64 n, int b, double* Q, i64 ldq, double* R, i64 ldr, int variant, const Work& w,
-                       cudaStream_t st, const Side* side = nullptr, bool adaptive = false) {
+                       cudaStream_t st, const Side* side = nullptr, bool adaptive = false, HostIO* io = nullptr) {
   switch (variant) {
     case CQR_MCQR2GS:
-      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st, side, adaptive);
-    case CQR_CQR2GS:
+      return mcqr2gs_run(m, n, b, Q, ldq, R, ldr, w, st, side, adaptive, io);
+    case CQR_CQR2GS: {
       TRY(cudaMemsetAsync(w.R1, 0, sizeof(double) * n * n, st));
       TRY(cudaMemsetAsync(w.R2, 0, sizeof(double) * n * n, st));
-      TRY(cqrgs_run(m, n, b, Q, ldq, w.R1, n, w, st, side));
-      TRY(cqrgs_run(m, n, b, Q, ldq, w.R2, n, w, st, side));
+      {
+        TracePhase ph("cqrgs_pass", 0);
+        TRY(cqrgs_run(m, n, b, Q, ldq, w.R1, n, w, st, side));
+      }
+      {
+        TracePhase ph("cqrgs_pass", 1);
+        TRY(cqrgs_run(m, n, b, Q, ldq, w.R2, n, w, st, side));
+      }
+      TracePhase ph("r_update", -1);
       return nn_product(n, (int)n, (int)n, w.R2, n, w.R1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
-    case CQR_CQR2:
+    }
+    case CQR_CQR2: {
+      TracePhase ph("cqr2", -1);
       TRY(cqr_panel(m, (int)n, Q, ldq, w.S1, n, w, 0, 0, st));
       TRY(cqr_panel(m, (int)n, Q, ldq, w.S2, n, w, 0, 0, st));
       return nn_product(n, (int)n, (int)n, w.S2, n, w.S1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
-    case CQR_SCQR3:
+    }
+    case CQR_SCQR3: {
+      TracePhase ph("scqr3", -1);
       TRY(cqr_panel(m, (int)n, Q, ldq, w.R1, n, w, 0, 1, st));  // Alg. 5 step 1: sCQR
       TRY(cqr_panel(m, (int)n, Q, ldq, w.S1, n, w, 0, 0, st));  // step 2: CQR2
       TRY(cqr_panel(m, (int)n, Q, ldq, w.S2, n, w, 0, 0, st));
       TRY(nn_product(n, (int)n, (int)n, w.S2, n, w.S1, n, w.R2, n, 1.0, 0, 1, 1, w.status, st));
       return nn_product(n, (int)n, (int)n, w.R2, n, w.R1, n, R, ldr, 1.0, 0, 1, 1, w.status, st);
+    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -375,6 +457,25 @@ const Side* get_side() {
     g_side_ok[dev] = true;
   }
   return &g_side[dev];
+}
+
+// Per-device copy stream and events of cqr_factor_host; the enqueue of one
+// call holds the mutex (the events are shared).
+std::mutex g_io_mu;
+HostIO g_io[64];
+bool g_io_ok[64] = {};
+
+HostIO* get_io() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!g_io_ok[dev]) {
+    HostIO& h = g_io[dev];
+    if (cudaStreamCreateWithFlags(&h.cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    for (cudaEvent_t* e : {&h.fork, &h.in_done, &h.panel_done, &h.join})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    g_io_ok[dev] = true;
+  }
+  return &g_io[dev];
 }
 
 // Caller-registered allocator for calls made with workspace == NULL.
@@ -523,6 +624,104 @@ int cqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int panel_b, double
   return 0;
 }
 
+int cqr_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int panel_b, double* Q, int64_t ldq,
+                    double* R, int64_t ldr, int variant_flags, double* Qd, int64_t ldqd, double* Rd, int64_t ldrd,
+                    void* workspace, size_t ws_bytes, cqr_stream_t stream) {
+  const bool lookahead = (variant_flags & CQR_LOOKAHEAD) != 0;
+  const bool adaptive = (variant_flags & CQR_ADAPTIVE) != 0;
+  const bool emulated = (variant_flags & CQR_EMULATED) != 0;
+  const bool halving = (variant_flags & CQR_HALVE) != 0;
+  const int variant = variant_flags & ~(CQR_LOOKAHEAD | CQR_ADAPTIVE | CQR_EMULATED | CQR_HALVE);
+  if (m < 1 || m < n) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (variant < 0 || variant > 3) return -10;
+  if ((variant == CQR_CQR2 || variant == CQR_SCQR3) && n > CQR_MAX_PANEL) return -2;
+  const int b = resolve_panel(n, panel_b, variant);
+  if (panel_b < 0 || b < 1 || b > CQR_MAX_PANEL || n % b) return -5;
+  if (!Q) return -6;
+  if (ldq < m || ((const double*)Q == A && ldq != lda)) return -7;
+  if ((const double*)Q != A && overlaps(A, lda, m, n, Q, ldq)) return -6;
+  if (!R) return -8;
+  if (ldr < n) return -9;
+  if ((emulated || adaptive || halving) && variant != CQR_MCQR2GS) return -10;
+  if (halving && (emulated || lookahead)) return -10;
+  if (!Qd) return -13;
+  if (ldqd < m) return -14;
+  if (!Rd) return -15;
+  if (ldrd < n) return -16;
+  {  // Rd's extent (n x n, ldrd) against Qd's (m x n, ldqd)
+    const char *q0 = (const char*)Qd, *q1 = (const char*)(Qd + (n - 1) * ldqd + m);
+    const char *r0 = (const char*)Rd, *r1 = (const char*)(Rd + (n - 1) * ldrd + n);
+    if (q0 < r1 && r0 < q1) return -15;
+  }
+  const Layout L = make_layout(m, n, b, variant, emulated, halving);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!workspace) {
+    Allocator al;
+    if (!registered_allocator(&al)) return -11;
+    return with_allocated_workspace(al, L.total, st, true, [&](void* ws) {
+      return cqr_factor_host(m, n, A, lda, panel_b, Q, ldq, R, ldr, variant_flags, Qd, ldqd, Rd, ldrd, ws, L.total,
+                             stream);
+    });
+  }
+  if ((uintptr_t)workspace & 255) return -11;
+  if (ws_bytes < L.total) return -12;
+  Work w = bind(workspace, L);
+  if (emulated) w.oz = (char*)workspace + L.oz;
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_io_mu);
+  HostIO* io = get_io();
+  if (!io) return CQR_ERR_CUDA;
+  io->Qh = Q;
+  io->ldqh = ldq;
+  io->rest_pending = false;
+  // Alg. 9 overlaps; the other variants copy in, factor and copy out
+  const bool overlap = variant == CQR_MCQR2GS;
+  const i64 first = overlap ? b : n;
+  if (cudaMemsetAsync(w.status, 0, sizeof(int), st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (cudaMemset2DAsync(Rd, sizeof(double) * ldrd, 0, sizeof(double) * n, n, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (copy_cols(Qd, ldqd, A, lda, m, 0, first, cudaMemcpyHostToDevice, st) != cudaSuccess) return CQR_ERR_CUDA;
+  // the copy stream starts behind the first panel's copy (which it does not
+  // share the link with) and everything the caller enqueued before
+  if (cudaEventRecord(io->fork, st) != cudaSuccess || cudaStreamWaitEvent(io->cs, io->fork, 0) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  if (first < n) {
+    if (copy_cols(Qd, ldqd, A, lda, m, first, n - first, cudaMemcpyHostToDevice, io->cs) != cudaSuccess ||
+        cudaEventRecord(io->in_done, io->cs) != cudaSuccess)
+      return CQR_ERR_CUDA;
+    io->rest_pending = true;
+  }
+  HostIO* pio = overlap ? io : nullptr;
+  int b_final = b;
+  cudaError_t e;
+  if (halving) {
+    e = mcqr2gs_halving_run(m, n, b, Qd, ldqd, Rd, ldrd, w, st, adaptive, &b_final, pio);
+  } else if (lookahead && (variant == CQR_MCQR2GS || variant == CQR_CQR2GS)) {
+    std::lock_guard<std::mutex> lk2(g_side_mu);
+    const Side* side = get_side();
+    e = side ? factor_run(m, n, b, Qd, ldqd, Rd, ldrd, variant, w, st, side, adaptive, pio) : cudaErrorUnknown;
+  } else {
+    e = factor_run(m, n, b, Qd, ldqd, Rd, ldrd, variant, w, st, nullptr, adaptive, pio);
+  }
+  if (e != cudaSuccess) return CQR_ERR_CUDA;
+  if (io_wait_rest(io, st) != cudaSuccess) return CQR_ERR_CUDA;  // n == b: nothing waited for it
+  if (!overlap && copy_cols(Q, ldq, Qd, ldqd, m, 0, n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  // join the copy stream, then R
+  if (cudaEventRecord(io->join, io->cs) != cudaSuccess || cudaStreamWaitEvent(st, io->join, 0) != cudaSuccess)
+    return CQR_ERR_CUDA;
+  if (copy_cols(R, ldr, Rd, ldrd, n, 0, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return CQR_ERR_CUDA;
+  if (halving) {
+    if (cudaMemcpyAsync((char*)workspace + kPanelOffset, &b_final, sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return CQR_ERR_CUDA;
+  }
+  return 0;
+}
+
 int cqr_read_panel_width(const void* workspace, cqr_stream_t stream, int* panel_b) {
   if (!workspace || !panel_b) return -1;
   int h = 0;
@@ -600,6 +799,7 @@ int cqr_backward(int64_t m, int64_t n, const double* Q, int64_t ldq, const doubl
   double* rinv = (double*)(p + off);
   off = align256(off + sizeof(double) * n);
   double* part = (double*)(p + off);
+  TracePhase ph("backward", -1);
   cudaGetLastError();
   const int nn = (int)n;
   // G = Qbar^T Q
@@ -761,6 +961,7 @@ int cqr_factor_batched(int batch, const int64_t* m, const int64_t* n, const int6
   }
   if ((uintptr_t)workspace & 255) return -11;
   if (ws_bytes < cqr_batched_workspace_size(batch, m, n, panel_b, flags)) return -12;
+  TracePhase ph("batched", batch);
   if (persistent) {
     const int grid = batched_persistent_grid();
     int G = md.G;

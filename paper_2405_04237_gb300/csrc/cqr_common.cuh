@@ -143,4 +143,16 @@ enum KernelClass {
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, double flops, cudaStream_t st);
 
+// Phase ranges of the host-side enqueue (prof.cu): an NVTX range in the
+// domain "cqr" and, when registered, the cqr_set_trace callback, for the
+// lifetime of the object.  `name` must be a string literal.
+struct TracePhase {
+  TracePhase(const char* name, int panel);
+  ~TracePhase();
+  TracePhase(const TracePhase&) = delete;
+  TracePhase& operator=(const TracePhase&) = delete;
+  const char* name;
+  int panel;
+};
+
 }  // namespace cqr

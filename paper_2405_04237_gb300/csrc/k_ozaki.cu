@@ -588,6 +588,32 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Contraction length up to which every level sum of an update tile is below
+// 2^22 in magnitude (14 pairs x 225 x K < 2^22): then the FP32 integer f is
+// read exactly as bits(f + 1.5 * 2^23) - bits(1.5 * 2^23), one full-rate
+// FP32 add and integer arithmetic, instead of a quarter-rate conversion.
+constexpr int kMagicMaxK = 1312;
+static_assert(14 * 225 * kMagicMaxK < (1 << 22), "level sums below 2^22");
+constexpr float kMagicF = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;  // its encoding
+
+// g = sum_{l<7} s_l 16^l for the seven FP32 level sums v[0..6][j] (s_l
+// exact integers, |s_l| < 2^22): three partial sums in unsigned 32-bit
+// arithmetic (the offsets cancel modulo 2^32 and |s_0 + 16 s_1 + 256 s_2| <
+// 2^31, so the two's-complement reading is the value), then
+// g = lo + 2^12 mid + 2^24 s_6.
+__device__ __forceinline__ long long group_sum_magic(const uint32_t (&v)[7][8], int j) {
+  uint32_t b[7];
+#pragma unroll
+  for (int l = 0; l < 7; ++l) b[l] = __float_as_uint(__fadd_rn(__uint_as_float(v[l][j]), kMagicF));
+  const uint32_t off = 273u * (uint32_t)kMagicBits;  // modulo 2^32
+  const int lo = (int)(b[0] + 16u * b[1] + 256u * b[2] - off);
+  const int mid = (int)(b[3] + 16u * b[4] + 256u * b[5] - off);
+  const int top = (int)(b[6] - (uint32_t)kMagicBits);
+  return (long long)lo + ((long long)mid << 12) + ((long long)top << 24);
+}
+
+template <bool kMagic>
 __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a, int ntiles) {
   extern __shared__ uint8_t up_raw[];
   __shared__ __align__(8) uint64_t full_bar[kUpRing], empty_bar[kUpRing], acc_full, acc_empty, mma_done;
@@ -712,8 +738,12 @@ __global__ void __launch_bounds__(kUpThreads, 1) ozaki_tc_update_kernel(OzArgs a
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             long long acc = 0;
+            if (kMagic) {
+              acc = group_sum_magic(v, j);
+            } else {
 #pragma unroll
-            for (int l = 6; l >= 0; --l) acc = acc * 16 + __float2int_rz(__uint_as_float(v[l][j]));
+              for (int l = 6; l >= 0; --l) acc = acc * 16 + __float2int_rz(__uint_as_float(v[l][j]));
+            }
             if (grp) g1[c0 + j] = acc;
             else g0[c0 + j] = acc;
           }
@@ -773,7 +803,8 @@ __global__ void ozaki_reduce_kernel(const double* part, i64 nsub, int p, int q, 
 void up_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(ozaki_tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmem);
+    cudaFuncSetAttribute(ozaki_tc_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmem);
+    cudaFuncSetAttribute(ozaki_tc_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpSmem);
     done = true;
   }
 }
@@ -958,7 +989,11 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
       take_fault(1, a);
       const int ntiles = (rws / kTcM) * tiles_q;
       prof_begin(kUpdate, st);
-      ozaki_tc_update_kernel<<<(unsigned)(ntiles < kSMs ? ntiles : kSMs), kUpThreads, kUpSmem, st>>>(a, ntiles);
+      const unsigned grid = (unsigned)(ntiles < kSMs ? ntiles : kSMs);
+      if (nst * kStage <= kMagicMaxK)
+        ozaki_tc_update_kernel<true><<<grid, kUpThreads, kUpSmem, st>>>(a, ntiles);
+      else
+        ozaki_tc_update_kernel<false><<<grid, kUpThreads, kUpSmem, st>>>(a, ntiles);
       prof_end(kUpdate, 2.0 * (double)live * N * kc, st);
     }
   }

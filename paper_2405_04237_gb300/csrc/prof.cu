@@ -7,6 +7,9 @@
 // so a caller can state achieved FLOP/s per kernel class against the FP64
 // roofline.  Timing is off by default (events inside a stream capture would
 // become graph nodes; the factorisation itself never needs them).
+#include <nvtx3/nvToolsExt.h>
+#include <stdio.h>
+
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -35,7 +38,49 @@ thread_local int t_open = -1;
 const char* kNames[kNumClasses] = {"gram_syrk", "projection_tn", "split_reduce", "cholesky", "trsm", "update_gemm",
                                    "misc", "batched"};
 
+// Phase tracing: NVTX (a no-op unless a tool is attached) plus an optional
+// caller callback.
+std::mutex g_trace_mu;
+cqr_trace_fn g_trace = nullptr;
+void* g_trace_ctx = nullptr;
+
+nvtxDomainHandle_t trace_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("cqr");
+  return d;
+}
+
+void trace_emit(const char* name, int panel, int begin) {
+  cqr_trace_fn fn;
+  void* ctx;
+  {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    fn = g_trace;
+    ctx = g_trace_ctx;
+  }
+  if (fn) fn(name, panel, begin, ctx);
+}
+
 }  // namespace
+
+TracePhase::TracePhase(const char* n, int p) : name(n), panel(p) {
+  char msg[64];
+  if (panel >= 0)
+    snprintf(msg, sizeof msg, "%s %d", name, panel);
+  else
+    snprintf(msg, sizeof msg, "%s", name);
+  nvtxEventAttributes_t at = {};
+  at.version = NVTX_VERSION;
+  at.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  at.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  at.message.ascii = msg;
+  nvtxDomainRangePushEx(trace_domain(), &at);
+  trace_emit(name, panel, 1);
+}
+
+TracePhase::~TracePhase() {
+  trace_emit(name, panel, 0);
+  nvtxDomainRangePop(trace_domain());
+}
 
 void prof_begin(int cls, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -70,6 +115,13 @@ using namespace cqr;
 extern "C" {
 
 unsigned long long cqr_launch_count(void) { return g_launches.load(); }
+
+int cqr_set_trace(cqr_trace_fn fn, void* ctx) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace = fn;
+  g_trace_ctx = fn ? ctx : nullptr;
+  return 0;
+}
 
 int cqr_profile_enable(int capacity) {
   std::lock_guard<std::mutex> lk(g_mu);

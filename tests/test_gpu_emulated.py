@@ -43,6 +43,7 @@ def test_emulated_exact_dyadic(cuda_lib, m, n, b):
     (12000, 128, 32, 1e4),
     (50000, 256, 64, 1e15),
     (8000, 96, 24, 1e12),
+    (8192, 1536, 128, 1e5),   # re-orthogonalisation updates with K = jb > 1312: the F2I level-sum path
 ])
 def test_emulated_parity(cuda_lib, oracle, m, n, b, kappa):
     A = make_test_matrix(m, n, kappa, seed=5000 + m + n)

@@ -70,6 +70,47 @@ def test_factor_argument_codes(L):
     assert factor_rc(L, ws_bytes=need - 1) == -12              # workspace too small
 
 
+def factor_host_rc(L, m=1000, n=64, A=A_ADDR, lda=None, b=16, Q=Q_ADDR, ldq=None, R=R_ADDR, ldr=None, variant=MC,
+                   Qd=S_ADDR, ldqd=None, Rd=W_ADDR + (1 << 35), ldrd=None, ws=W_ADDR, ws_bytes=1 << 40):
+    lda = m if lda is None else lda
+    ldq = m if ldq is None else ldq
+    ldr = n if ldr is None else ldr
+    ldqd = m if ldqd is None else ldqd
+    ldrd = n if ldrd is None else ldrd
+    return L.cqr_factor_host(m, n, vp(A), lda, b, vp(Q), ldq, vp(R), ldr, variant, vp(Qd), ldqd, vp(Rd), ldrd,
+                             vp(ws), ws_bytes, vp(0))
+
+
+def test_factor_host_argument_codes(L):
+    """cqr_factor_host: the codes of cqr_factor for arguments 1-10 (host
+    A, Q, R), then the device buffers Qd (13, 14) and Rd (15, 16)."""
+    assert factor_host_rc(L, m=10, n=16) == -1
+    assert factor_host_rc(L, n=0) == -2
+    assert factor_host_rc(L, m=9000, n=1024, variant=C2) == -2
+    assert factor_host_rc(L, A=0) == -3
+    assert factor_host_rc(L, lda=999) == -4
+    assert factor_host_rc(L, b=5) == -5
+    assert factor_host_rc(L, Q=0) == -6
+    assert factor_host_rc(L, Q=A_ADDR + 8 * 100) == -6          # host Q overlaps host A
+    assert factor_host_rc(L, ldq=999) == -7
+    assert factor_host_rc(L, Q=A_ADDR, lda=1000, ldq=1024) == -7  # in place on the host with ldq != lda
+    assert factor_host_rc(L, R=0) == -8
+    assert factor_host_rc(L, ldr=63) == -9
+    assert factor_host_rc(L, variant=4) == -10
+    assert factor_host_rc(L, variant=CG | _capi.HALVE) == -10
+    assert factor_host_rc(L, variant=MC | _capi.HALVE | _capi.LOOKAHEAD) == -10
+    assert factor_host_rc(L, Qd=0) == -13
+    assert factor_host_rc(L, ldqd=999) == -14
+    assert factor_host_rc(L, Rd=0) == -15
+    assert factor_host_rc(L, Rd=S_ADDR + 8 * 5000) == -15        # Rd inside Qd
+    assert factor_host_rc(L, Rd=S_ADDR - 8 * 100) == -15         # Rd's tail reaches into Qd
+    assert factor_host_rc(L, ldrd=63) == -16
+    assert factor_host_rc(L, ws=0) == -11                        # no registered allocator
+    assert factor_host_rc(L, ws=W_ADDR + 8) == -11
+    need = L.cqr_workspace_size(1000, 64, 16, MC)
+    assert factor_host_rc(L, ws_bytes=need - 1) == -12
+
+
 def test_halving_workspace_covers_every_width(L):
     """The adaptive width's workspace holds the partial sums of every width
     the chain b, b/2, ..., 1 can reach, so it is never smaller than the
