@@ -444,11 +444,15 @@ def run_ours(args, dist, rank, world):
     dev = torch.cuda.current_device()
     m, n, kappa = args.m, args.n, args.kappa
     b = args.panel or autotune(m, n, "mcqr2gs", kappa, cands=[c for c in PANEL_CANDIDATES if n % c == 0 and n // c >= 3])
-    A = make_test_matrix_cuda(m, n, kappa, SEED_FULL + 100 * rank)
+    # Q, R and the workspace first: the generator's dense QR of a 2^23 x 1024
+    # Gaussian leaves device memory in a state where a buffer allocated after
+    # it has regions the copy engines reach at a tenth of their rate (measured
+    # on GB300), and Q is the device buffer of the host-buffer leg below.
     Q = P.empty_colmajor(m, n, "cuda")
     R = P.empty_colmajor(n, n, "cuda")
     emu = bool(args.emulated)
     ws = torch.empty(P.workspace_size(m, n, b, "mcqr2gs", emulated=emu), dtype=torch.uint8, device="cuda")
+    A = make_test_matrix_cuda(m, n, kappa, SEED_FULL + 100 * rank)
     torch.cuda.synchronize()
     for i in range(args.warmup):
         P.factor(A, b, out=(Q, R), workspace=ws, check=(i == 0), emulated=emu)

@@ -154,66 +154,111 @@ __device__ __forceinline__ i64 plane_off(i64 col, int half) {
 
 // ---------------------------------------------------------------------------
 // Column splitting: X (rows r0 .. r0 + nsub*kSub of an m x c matrix) ->
-// planes.  Grid (c, nsub), columns fastest: two neighbouring columns share
-// every 32-byte sector of the layout, so they are split together and the
-// sectors are completed while still in L2.  256 threads; thread t handles rows 16t .. 16t+15
-// of the sub-chunk (half t & 1 of stage t / 2).  Tiles of T columns; plane
-// block (s, tile, st, i) starts at byte
+// planes.  Grid (ceil(c / 8), nsub), 256 threads: block (g, s) takes the
+// 8-column group g of the layout (columns 8g .. 8g+7) over sub-chunk s, so
+// that for each stage and plane its digits form one contiguous 256-byte run
+// (8 columns x 32 indices).  Lane l of warp w handles column 8g + (l & 7),
+// half (l >> 3) & 1 (indices 0..15 or 16..31 of a stage) of stages
+// 16 it + 2 w + (l >> 4), it = 0..7: every warp store writes two whole
+// 256-byte runs.  Two passes over the sub-chunk: the column maxima (scales),
+// then the digits; the second pass re-reads from L2 (at most two blocks, 2 x
+// 256 KiB, per SM).  Tiles of T columns (T a multiple of 8); plane block
+// (s, tile, st, i) starts at byte
 // (((s * ntile + tile) * kStagesPerSub + st) * kPlanes + i) * T * 32 with
-// ntile = ceil(c / T); exps: [s * c + col].
-__global__ void __launch_bounds__(256) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c, int T,
-                                                          uint8_t* planes, int* exps, const int* status) {
+// ntile = ceil(c / T); exps: [s * c + col].  Columns past c of the last
+// group are written as zero digits (the tile padding; never read).
+// 16 consecutive entries xc[row .. row+15] (zero past m or for a column past
+// c); 16-byte loads when the address allows (an odd leading dimension puts
+// every other column off the 16-byte grid).
+__device__ __forceinline__ void load16(const double* xc, i64 row, i64 m, bool colok, unsigned long long (&bits)[16]) {
+  if (colok && row + 15 < m && ((reinterpret_cast<uintptr_t>(xc + row) & 15) == 0)) {
+    const double2* p = reinterpret_cast<const double2*>(xc + row);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double2 v = __ldg(p + k);
+      bits[2 * k] = (unsigned long long)__double_as_longlong(v.x);
+      bits[2 * k + 1] = (unsigned long long)__double_as_longlong(v.y);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      bits[k] = (unsigned long long)__double_as_longlong((colok && row + k < m) ? xc[row + k] : 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) ozaki_split_kernel(const double* X, i64 ldx, i64 m, i64 r0, int c, int T,
+                                                             uint8_t* planes, int* exps, const int* status) {
   if (status && *status) return;
-  const int col = blockIdx.x, s = blockIdx.y, t = threadIdx.x;
-  const i64 base = r0 + (i64)s * kSub + 16 * t;
-  const double* xc = X + (i64)col * ldx;
-  unsigned long long bits[16];
+  const int g = blockIdx.x, s = blockIdx.y, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int cl = lane & 7, half = (lane >> 3) & 1, so = lane >> 4;
+  const int col = 8 * g + cl;
+  const bool colok = col < c;
+  const i64 base = r0 + (i64)s * kSub;
+  const double* xc = X + (i64)(colok ? col : 0) * ldx;
+  // pass 1: the column's largest exponent (zeros and subnormals do not set the scale) and Inf/NaN
   int emax = -2000;
   bool bad = false;
+#pragma unroll 1
+  for (int it = 0; it < 8; ++it) {
+    const int st = 16 * it + 2 * warp + so;
+    unsigned long long bits[16];
+    load16(xc, base + st * kStage + 16 * half, m, colok, bits);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const i64 r = base + k;
-    const double v = r < m ? xc[r] : 0.0;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    bits[k] = b;
-    const int E = (int)((b >> 52) & 0x7FF);
-    if (E == 0x7FF) bad = true;
-    if (E != 0 && E > emax) emax = E;  // zeros and subnormals do not set the scale
+    for (int k = 0; k < 16; ++k) {
+      const int E = (int)((bits[k] >> 52) & 0x7FF);
+      if (E == 0x7FF) bad = true;
+      if (E != 0 && E > emax) emax = E;
+    }
   }
-  __shared__ int red_max[256 / 32];
-  __shared__ int red_bad[256 / 32];
-  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-  const int anybad = __any_sync(0xffffffffu, bad);
-  if ((t & 31) == 0) {
-    red_max[t >> 5] = emax;
-    red_bad[t >> 5] = anybad;
+  // lanes l, l ^ 8, l ^ 16, l ^ 24 hold the same column
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 8));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 16));
+  int anyb = bad ? 1 : 0;
+  anyb |= __shfl_xor_sync(0xffffffffu, anyb, 8);
+  anyb |= __shfl_xor_sync(0xffffffffu, anyb, 16);
+  __shared__ int red_max[8][8], red_bad[8][8];
+  __shared__ int e_col[8];
+  if (lane < 8) {
+    red_max[warp][lane] = emax;
+    red_bad[warp][lane] = anyb;
   }
   __syncthreads();
-  int E_max = -2000, B = 0;
-  for (int w = 0; w < 256 / 32; ++w) {
-    E_max = max(E_max, red_max[w]);
-    B |= red_bad[w];
+  if (t < 8) {
+    int E_max = -2000, B = 0;
+    for (int w = 0; w < 8; ++w) {
+      E_max = max(E_max, red_max[w][t]);
+      B |= red_bad[w][t];
+    }
+    // |x| < 2^(E - 1022) for biased exponent E; scale e with |x| < 2^e: e = E_max - 1022
+    const int e = B ? kExpBad : (E_max < 0 ? kExpZero : E_max - 1022);
+    e_col[t] = e;
+    if (8 * g + t < c) exps[(i64)s * c + 8 * g + t] = e;
   }
-  // |x| < 2^(E - 1022) for biased exponent E; scale e with |x| < 2^e: e = E_max - 1022
-  const int e = B ? kExpBad : (E_max < 0 ? kExpZero : E_max - 1022);
-  if (t == 0) exps[(i64)s * c + col] = e;
-  uint32_t words[kPlanes][4];
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const unsigned long long b4[4] = {bits[4 * g], bits[4 * g + 1], bits[4 * g + 2], bits[4 * g + 3]};
-    uint32_t w[kPlanes];
-    digits4(b4, e, w);
-#pragma unroll
-    for (int i = 0; i < kPlanes; ++i) words[i][g] = w[i];
-  }
-  const int st = t >> 1, half = t & 1;
+  __syncthreads();
+  const int e = e_col[cl];
+  // pass 2: digits, one 16-byte granule per plane
   const int ntile = (c + T - 1) / T;
-  uint8_t* dst = planes + (((i64)s * ntile + col / T) * kStagesPerSub + st) * kPlanes * T * kStage +
-                 plane_off(col % T, half);
+  uint8_t* dst0 = planes + ((i64)s * ntile + col / T) * kStagesPerSub * kPlanes * T * kStage + plane_off(col % T, half);
+#pragma unroll 1
+  for (int it = 0; it < 8; ++it) {
+    const int st = 16 * it + 2 * warp + so;
+    unsigned long long bits[16];
+    load16(xc, base + st * kStage + 16 * half, m, colok, bits);
+    uint32_t words[kPlanes][4];
 #pragma unroll
-  for (int i = 0; i < kPlanes; ++i) {
-    uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
-    *reinterpret_cast<uint4*>(dst + (i64)i * T * kStage) = v;
+    for (int q = 0; q < 4; ++q) {
+      const unsigned long long b4[4] = {bits[4 * q], bits[4 * q + 1], bits[4 * q + 2], bits[4 * q + 3]};
+      uint32_t w[kPlanes];
+      digits4(b4, e, w);
+#pragma unroll
+      for (int i = 0; i < kPlanes; ++i) words[i][q] = w[i];
+    }
+    uint8_t* dst = dst0 + (i64)st * kPlanes * T * kStage;
+#pragma unroll
+    for (int i = 0; i < kPlanes; ++i) {
+      uint4 v = make_uint4(words[i][0], words[i][1], words[i][2], words[i][3]);
+      *reinterpret_cast<uint4*>(dst + (i64)i * T * kStage) = v;
+    }
   }
 }
 
@@ -895,11 +940,11 @@ cudaError_t tn_product_emulated(i64 m, int p, int q, const double* X, i64 ldx, c
   for (i64 r0 = 0; r0 < m; r0 += ch) {
     const i64 nsub = ((m - r0 < ch ? m - r0 : ch) + kSub - 1) / kSub;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)p, (unsigned)nsub), 256, 0, st>>>(X, ldx, m, r0, p, kTcM, px, ex, status);
+    ozaki_split_kernel<<<dim3((unsigned)((p + 7) / 8), (unsigned)nsub), 256, 0, st>>>(X, ldx, m, r0, p, kTcM, px, ex, status);
     prof_end(kMisc, 0.0, st);
     if (!same) {
       prof_begin(kMisc, st);
-      ozaki_split_kernel<<<dim3((unsigned)q, (unsigned)nsub), 256, 0, st>>>(Y, ldy, m, r0, q, kTcN, py, ey, status);
+      ozaki_split_kernel<<<dim3((unsigned)((q + 7) / 8), (unsigned)nsub), 256, 0, st>>>(Y, ldy, m, r0, q, kTcN, py, ey, status);
       prof_end(kMisc, 0.0, st);
     }
     OzArgs a{};
@@ -965,7 +1010,7 @@ cudaError_t nn_update_emulated(i64 M, int N, int K, const double* X, i64 ldx, co
     const int kc = (int)(K - k0 < kSub ? K - k0 : kSub);
     const int nst = (kc + kStage - 1) / kStage;
     prof_begin(kMisc, st);
-    ozaki_split_kernel<<<dim3((unsigned)N, 1u), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, kTcN, py, ey, status);
+    ozaki_split_kernel<<<dim3((unsigned)((N + 7) / 8), 1u), 256, 0, st>>>(Y, ldy, k0 + kc, k0, N, kTcN, py, ey, status);
     prof_end(kMisc, 0.0, st);
     for (i64 r0 = 0; r0 < M; r0 += rows) {
       const i64 live = M - r0 < rows ? M - r0 : rows;
