@@ -96,6 +96,10 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false, bool
   size_t oz = 0;
   if (emulated && variant == CQR_MCQR2GS) {  // Gram matrices; products with Y (b x w) and Z (jb x b) of Alg. 9
     oz = ozaki_workspace_bytes(m, b, b);
+    for (int c0 = kTrsmMaxB; c0 < b; c0 += kTrsmMaxB) {  // the triangular solves' coupling products
+      const size_t d = ozaki_nn_workspace_bytes(m, b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB, c0);
+      if (d > oz) oz = d;
+    }
     for (i64 j = 1; j * b < n; ++j) {
       const size_t d[4] = {ozaki_workspace_bytes(m, b, (int)(n - j * b)), ozaki_workspace_bytes(m, (int)(j * b), b),
                            ozaki_nn_workspace_bytes(m, (int)(n - j * b), b),
@@ -142,12 +146,17 @@ Work bind(void* ws, const Layout& L) {
 
 // X := X U^{-1} for any width: kTrsmMaxB-column blocks, the coupling between
 // blocks applied as an FMA update in ascending column order (so each element
-// sees the same operation sequence as plain substitution).
+// sees the same operation sequence as plain substitution).  With `oz` (the
+// emulated variant) the coupling X_2 -= X_1 U_12 is one of the m-row
+// products and runs on the tensor cores like the others; the substitutions
+// within a block stay FP64.
 cudaError_t trsm_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
-                     const int* status, cudaStream_t st, const int* skip = nullptr) {
+                     const int* status, cudaStream_t st, const int* skip = nullptr, void* oz = nullptr) {
   for (int c0 = 0; c0 < b; c0 += kTrsmMaxB) {
     const int cb = b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB;
-    if (c0 > 0)
+    if (c0 > 0 && oz)
+      TRY(nn_update_emulated(m, cb, c0, X, ldx, U + (i64)c0 * ldu, ldu, X + (i64)c0 * ldx, ldx, oz, status, st));
+    else if (c0 > 0)
       TRY(nn_product(m, cb, c0, X, ldx, U + (i64)c0 * ldu, ldu, X + (i64)c0 * ldx, ldx, -1.0, 1, 0, 0, status, st));
     TRY(trsm_rows(m, cb, X + (i64)c0 * ldx, ldx, U + c0 + (i64)c0 * ldu, ldu, rinv + c0, status, st, skip));
   }
@@ -181,7 +190,7 @@ cudaError_t cqr_panel(i64 m, int b, double* X, i64 ldx, double* U, i64 ldu, cons
   else
     TRY(tn_product(m, b, b, X, ldx, X, ldx, 1, w.part, w.W, b, w.status, st));
   TRY(chol_factor(b, w.W, b, U, ldu, w.rinv, col0, w.status, shift, m, st, skip));
-  TRY(trsm_any(m, b, X, ldx, U, ldu, w.rinv, w.status, st, skip));
+  TRY(trsm_any(m, b, X, ldx, U, ldu, w.rinv, w.status, st, skip, w.oz));
   return cudaSuccess;
 }
 
