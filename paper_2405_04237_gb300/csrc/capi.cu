@@ -20,6 +20,11 @@ struct Layout {
   size_t status, skip, panel, W, S1, S2, rinv, Z, R1, R2, part, oz, total;
 };
 
+// Substitution block width of the emulated variant: its coupling products
+// run on the tensor cores, so narrower blocks move FP64 substitution work
+// (b * blk per row) into them.
+constexpr int kTrsmEmuB = 32;
+
 // Offsets of the words cqr_read_status and cqr_read_panel_width read.
 constexpr size_t kStatusOffset = 0, kPanelOffset = 512;
 
@@ -96,8 +101,8 @@ Layout make_layout(i64 m, i64 n, int b, int variant, bool emulated = false, bool
   size_t oz = 0;
   if (emulated && variant == CQR_MCQR2GS) {  // Gram matrices; products with Y (b x w) and Z (jb x b) of Alg. 9
     oz = ozaki_workspace_bytes(m, b, b);
-    for (int c0 = kTrsmMaxB; c0 < b; c0 += kTrsmMaxB) {  // the triangular solves' coupling products
-      const size_t d = ozaki_nn_workspace_bytes(m, b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB, c0);
+    for (int c0 = kTrsmEmuB; c0 < b; c0 += kTrsmEmuB) {  // the triangular solves' coupling products
+      const size_t d = ozaki_nn_workspace_bytes(m, b - c0 < kTrsmEmuB ? b - c0 : kTrsmEmuB, c0);
       if (d > oz) oz = d;
     }
     for (i64 j = 1; j * b < n; ++j) {
@@ -152,8 +157,9 @@ Work bind(void* ws, const Layout& L) {
 // within a block stay FP64.
 cudaError_t trsm_any(i64 m, int b, double* X, i64 ldx, const double* U, i64 ldu, const double* rinv,
                      const int* status, cudaStream_t st, const int* skip = nullptr, void* oz = nullptr) {
-  for (int c0 = 0; c0 < b; c0 += kTrsmMaxB) {
-    const int cb = b - c0 < kTrsmMaxB ? b - c0 : kTrsmMaxB;
+  const int blk = oz ? kTrsmEmuB : kTrsmMaxB;
+  for (int c0 = 0; c0 < b; c0 += blk) {
+    const int cb = b - c0 < blk ? b - c0 : blk;
     if (c0 > 0 && oz)
       TRY(nn_update_emulated(m, cb, c0, X, ldx, U + (i64)c0 * ldu, ldu, X + (i64)c0 * ldx, ldx, oz, status, st));
     else if (c0 > 0)
