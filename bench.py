@@ -515,8 +515,8 @@ def run_ours(args, dist, rank, world):
     # inside the timed region (overlapped with the panels by the library)
     e2e = None
     if not args.no_e2e:
-        # A pinned guard block first.  Measured on GB300 after the generator's
-        # dense QR: the first ~8 GB of the next large pinned allocation copy at
+        # A pinned guard block first.  Measured on GB300: in most runs the
+        # first ~8 GB of a process's first large pinned allocation copy at
         # 20-80 GB/s instead of 210, and the first panel of A, whose copy the
         # factorisation waits for, would sit there; behind a guard it copies
         # at full rate.  The guard is touched once by a copy each way, as in
