@@ -415,9 +415,9 @@ def bench_emulated(P, A, Q, R, b, args, flops, t_native):
     orth, res = accuracy(A, Q, R)
     return {"value": flops / t / 1e12, "unit": "TFLOP/s (FP64-equivalent, 4 m n^2 / t)", "ms_per_step": 1e3 * t,
             "speedup_vs_native": t_native / t, "orth_fro": orth, "resid_rel": res, "status": status,
-            "what": "Gram matrices, projections and updates on the tcgen05 FP8 tensor cores (14-digit Ozaki "
-                    "splitting, exact FP32 level sums in TMEM); Cholesky factorisations and triangular solves "
-                    "native FP64"}
+            "what": "Gram matrices, projections, updates and the triangular solves' coupling products on the "
+                    "tcgen05 FP8 tensor cores (14-digit Ozaki splitting, exact FP32 level sums in TMEM); "
+                    "Cholesky factorisations and the solves' 32-column substitutions native FP64"}
 
 
 # DRAM bytes per launch of the update kernel class, from one ncu capture

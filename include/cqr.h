@@ -83,7 +83,10 @@ enum cqr_variant {
  * exactly (FP32 accumulation of integers < 2^24) and recombined with one
  * rounding.  Not FP64 arithmetic, but FP64-accurate: the truncation drops
  * terms below about 2^-52 of the scales' product.  The Cholesky
- * factorisations and triangular solves stay native FP64.  The update runs
+ * factorisations and the substitutions of the triangular solves stay native
+ * FP64; a solve runs in 32-column substitution blocks, and the products that
+ * couple the blocks (X_2 -= X_1 U_12, m rows) are emulated like the other
+ * m-row products.  The update runs
  * unsplit on the caller's stream, so CQR_LOOKAHEAD has no effect with this
  * flag.  The workspace grows (cqr_workspace_size with the flag) by the digit
  * planes of one row chunk (about 1 GiB) and one FP64 partial per 4096 rows. */
