@@ -472,7 +472,9 @@ int cqr_probe_fp64(int kind, int iters, double* gflops, double* flop_per_clk_sm,
  * a tool correlates them with the launches inside each range).
  * cqr_set_trace(fn, ctx): also call fn(phase, panel, begin, ctx) on the
  *   enqueueing thread at the start (begin = 1) and end (begin = 0) of every
- *   phase; fn = NULL unregisters.  Returns 0.
+ *   phase; fn = NULL unregisters.  fn runs while the call may hold the
+ *   library's per-device stream locks, so it must not call the library (it
+ *   may record CUDA events, as a timeline tool does).  Returns 0.
  */
 typedef void (*cqr_trace_fn)(const char* phase, int panel, int begin, void* ctx);
 int cqr_set_trace(cqr_trace_fn fn, void* ctx);

@@ -702,10 +702,16 @@ int cqr_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int pane
   // share the link with) and everything the caller enqueued before
   if (cudaEventRecord(io->fork, st) != cudaSuccess || cudaStreamWaitEvent(io->cs, io->fork, 0) != cudaSuccess)
     return CQR_ERR_CUDA;
+  // From here on an error still joins the copy stream into `stream`, so that
+  // no copy of the caller's host buffers outlives the call's stream work.
+  auto fail = [&]() {
+    if (cudaEventRecord(io->join, io->cs) == cudaSuccess) cudaStreamWaitEvent(st, io->join, 0);
+    return CQR_ERR_CUDA;
+  };
   if (first < n) {
     if (copy_cols(Qd, ldqd, A, lda, m, first, n - first, cudaMemcpyHostToDevice, io->cs) != cudaSuccess ||
         cudaEventRecord(io->in_done, io->cs) != cudaSuccess)
-      return CQR_ERR_CUDA;
+      return fail();
     io->rest_pending = true;
   }
   HostIO* pio = overlap ? io : nullptr;
@@ -720,10 +726,9 @@ int cqr_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int pane
   } else {
     e = factor_run(m, n, b, Qd, ldqd, Rd, ldrd, variant, w, st, nullptr, adaptive, pio);
   }
-  if (e != cudaSuccess) return CQR_ERR_CUDA;
-  if (io_wait_rest(io, st) != cudaSuccess) return CQR_ERR_CUDA;  // n == b: nothing waited for it
-  if (!overlap && copy_cols(Q, ldq, Qd, ldqd, m, 0, n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return CQR_ERR_CUDA;
+  if (e != cudaSuccess) return fail();
+  if (io_wait_rest(io, st) != cudaSuccess) return fail();  // n == b: nothing waited for it
+  if (!overlap && copy_cols(Q, ldq, Qd, ldqd, m, 0, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail();
   // join the copy stream, then R
   if (cudaEventRecord(io->join, io->cs) != cudaSuccess || cudaStreamWaitEvent(st, io->join, 0) != cudaSuccess)
     return CQR_ERR_CUDA;
