@@ -29,7 +29,8 @@ def test_emulated_exact_golden(cuda_lib):
         assert np.array_equal(R, R0) and np.array_equal(Q, Q0), b
 
 
-@pytest.mark.parametrize("m,n,b", [(4096, 64, 16), (16384, 128, 32), (1024, 12, 3)])
+@pytest.mark.parametrize("m,n,b", [(4096, 64, 16), (16384, 128, 32), (1024, 12, 3),
+                                   (4096, 96, 48)])  # b = 48: a 16-column substitution block after a 32-column one
 def test_emulated_exact_dyadic(cuda_lib, m, n, b):
     A, Q0, R0 = exact_qr_case(m, n, seed=m + n)
     Q, R = gpu_factor(cuda_lib, A, b, emulated=True)
@@ -44,6 +45,7 @@ def test_emulated_exact_dyadic(cuda_lib, m, n, b):
     (50000, 256, 64, 1e15),
     (8000, 96, 24, 1e12),
     (8192, 1536, 128, 1e5),   # re-orthogonalisation updates with K = jb > 1312: the F2I level-sum path
+    (30011, 96, 48, 1e6),     # ragged m; the solve's coupling product has N = 16 (a partial column tile)
 ])
 def test_emulated_parity(cuda_lib, oracle, m, n, b, kappa):
     A = make_test_matrix(m, n, kappa, seed=5000 + m + n)
