@@ -89,7 +89,7 @@ enum cqr_variant {
  * m-row products.  The update runs
  * unsplit on the caller's stream, so CQR_LOOKAHEAD has no effect with this
  * flag.  The workspace grows (cqr_workspace_size with the flag) by the digit
- * planes of one row chunk (about 1 GiB) and one FP64 partial per 4096 rows. */
+ * planes of one row chunk (1 to 2 GiB) and one FP64 partial per 4096 rows. */
 #define CQR_EMULATED 0x400
 
 /* Flag OR-ed into `variant` of cqr_factor and cqr_workspace_size (MCQR2GS

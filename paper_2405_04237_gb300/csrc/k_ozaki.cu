@@ -890,11 +890,23 @@ inline i64 oz_nn_rows(int nst) {
 
 }  // namespace
 
-// Rows per splitting chunk of a projection: planes of one chunk take about 1 GiB.
+// Rows per splitting chunk of a projection: planes of one chunk take 1 to
+// 2 GiB.  A launch has (column tiles) x (sub-chunks) blocks of equal length,
+// one per SM, so a partly filled last wave costs a whole one; of the
+// sub-chunk counts between the 1 GiB budget and twice it, the one with the
+// fewest waves per sub-chunk is taken (the smallest among equals).
 i64 oz_chunk_rows(int p, int q) {
-  i64 rows = ((i64)1 << 30) / ((i64)kPlanes * (round_up(p, kTcM) + round_up(q, kTcN)));
-  rows = (rows / kSub) * kSub;
-  return rows < kSub ? kSub : rows;
+  const i64 cpx = round_up(p, kTcM), cpy = round_up(q, kTcN);
+  i64 base = ((i64)1 << 30) / ((i64)kPlanes * (cpx + cpy) * kSub);
+  if (base < 1) base = 1;
+  const i64 tiles = (cpx / kTcM) * (cpy / kTcN);
+  i64 best = base;
+  for (i64 n = base + 1; n <= 2 * base; ++n) {
+    // waves(n) / n < waves(best) / best, in integers
+    const i64 wn = (tiles * n + kSMs - 1) / kSMs, wb = (tiles * best + kSMs - 1) / kSMs;
+    if (wn * best < wb * n) best = n;
+  }
+  return best * kSub;
 }
 
 size_t ozaki_workspace_bytes(i64 m, int p, int q) {
