@@ -521,11 +521,24 @@ def run_ours(args, dist, rank, world):
         # factorisation waits for, would sit there; behind a guard it copies
         # at full rate.  The guard is touched once by a copy each way, as in
         # the measurement.
-        guard_n = min(16 << 27, 2 * m * b)  # at most 16 GiB of FP64
-        guard = torch.empty(guard_n, dtype=torch.float64, pin_memory=True)
-        Ah = P.empty_colmajor_pinned(m, n)
-        Qh = P.empty_colmajor_pinned(m, n)
-        Rh = P.empty_colmajor_pinned(n, n)
+        guard_n = 16 << 27  # 16 GiB of FP64: the slow region is ~8 GB whatever the matrix size
+        why = ""
+        try:
+            guard = torch.empty(guard_n, dtype=torch.float64, pin_memory=True)
+            Ah = P.empty_colmajor_pinned(m, n)
+            Qh = P.empty_colmajor_pinned(m, n)
+            Rh = P.empty_colmajor_pinned(n, n)
+        except (RuntimeError, MemoryError) as ex:  # not enough page-locked host memory
+            guard = Ah = Qh = Rh = None
+            why = str(ex).splitlines()[0][:160] if str(ex) else type(ex).__name__
+        # every rank takes the same decision before the barrier below
+        if allreduce_max(dist, 1.0 if why else 0.0) > 0.0:
+            e2e = {"value": None, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * m * n,
+                   "d2h_bytes_per_step": 8 * (m * n + n * n),
+                   "unavailable": "page-locked host buffers could not be allocated on every rank"
+                                  + (f" ({why})" if why else "")}
+            del guard, Ah, Qh, Rh
+    if not args.no_e2e and e2e is None:
         Ah.copy_(A)
         Qh.copy_(A)
         gd = torch.empty(guard_n, dtype=torch.float64, device="cuda")

@@ -74,7 +74,7 @@ def main(argv=None) -> None:
     # a pinned guard block first: on GB300 the first ~8 GB of a process's
     # first large pinned allocation often copy at a tenth of the full rate,
     # which is a property of that host memory, not of the copies' schedule
-    guard = torch.empty(min(16 << 27, 2 * m * b), dtype=torch.float64, pin_memory=True) if args.guard else None
+    guard = torch.empty(16 << 27, dtype=torch.float64, pin_memory=True) if args.guard else None
     Ah, Qh, Rh = empty_colmajor_pinned(m, n), empty_colmajor_pinned(m, n), empty_colmajor_pinned(n, n)
     Ah.copy_(A)
     Qh.copy_(A)
